@@ -1,0 +1,165 @@
+/*
+ * h2ulv.h -- C ABI of the GB300 (sm_103a) dependency-free H^2-ULV solver.
+ *
+ * The method is the one of Ma, Deshmukh and Yokota, "Scalable Linear Time
+ * Dense Direct Solver for 3-D Problems Without Trailing Sub-Matrix
+ * Dependencies" (arXiv 2208.10907): a dense kernel matrix A_ij = K(x_i, x_j)
+ * over a point cloud is compressed as an H^2 matrix with strong
+ * admissibility (Sec. I), the fill-ins of the dense-block factorization are
+ * pre-computed and folded into the shared bases (Sec. III-B/C, eq. fillu and
+ * eq. fillv), and every level is then factored box by box without trailing
+ * sub-matrix dependencies (eq. rs, eq. ss, eq. lu ... eq. BLR2final).
+ *
+ * Conventions for every entry point:
+ *   - All functions return an h2_status; nothing throws across the ABI.  On
+ *     error, h2_last_error() returns a thread-local message.
+ *   - Array arguments are plain pointers that may point to host memory or
+ *     to device memory of the current CUDA device; the library detects which
+ *     (cudaPointerGetAttributes) and copies host buffers itself.
+ *   - The caller owns every array it passes; the library copies what it
+ *     keeps.  The library owns all factor storage through the handle until
+ *     h2_destroy().
+ *   - Work is issued on the stream given to h2_construct (NULL = legacy
+ *     default stream).  Calls that return values to host memory synchronise
+ *     that stream.
+ *   - Vectors are in the caller's point order (the tree permutation is
+ *     internal); multiple right-hand sides are column-major with leading
+ *     dimension ld >= N.
+ */
+#ifndef H2ULV_H
+#define H2ULV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  H2_OK = 0,
+  H2_ERR_ARG = 1,           /* invalid argument (null pointer, size, tolerance) */
+  H2_ERR_NONFINITE = 2,     /* NaN or Inf in the points or the right-hand side  */
+  H2_ERR_OOM = 3,           /* device allocation failed                         */
+  H2_ERR_BUDGET = 4,        /* the memory plan exceeds hbm_budget_bytes         */
+  H2_ERR_SINGULAR = 5,      /* zero pivot in a redundant-block or root LU       */
+  H2_ERR_RANK_CAP = 6,      /* reserved: rank cap violated by a predicted size  */
+  H2_ERR_NOT_CONVERGED = 7, /* refinement stopped at max_iter above the target  */
+  H2_ERR_DEVICE = 8,        /* CUDA error (message in h2_last_error)            */
+  H2_ERR_STATE = 9,         /* call out of order (e.g. solve before factor)     */
+  H2_ERR_NOT_SPD = 10       /* Cholesky pivot <= 0 in the SPD path              */
+} h2_status;
+
+/* Kernel functions (Sec. IV: Laplace Green's function; Sec. V: Yukawa).
+ * The point singularity of 1/(4 pi r) is regularised:
+ *   H2_K_LAPLACE : K = 1 / (r + delta)
+ *   H2_K_YUKAWA  : K = exp(-kappa r) / (r + delta)
+ *   H2_K_MATERN32: K = (1 + sqrt(3) r / ell) exp(-sqrt(3) r / ell), plus
+ *                  nugget on the diagonal (r == 0). */
+typedef enum { H2_K_LAPLACE = 0, H2_K_YUKAWA = 1, H2_K_MATERN32 = 2 } h2_kernel_kind;
+
+typedef struct {
+  int32_t kind;    /* h2_kernel_kind */
+  double delta;    /* regulariser of 1/r, e.g. 1e-3 */
+  double kappa;    /* Yukawa decay, e.g. 1 */
+  double ell;      /* Matern length scale, e.g. 0.1 */
+  double nugget;   /* Matern diagonal shift, e.g. 1e-4 */
+} h2_kernel;
+
+/* Construction options (Sec. I admissibility, Sec. II-A rank tolerance,
+ * Sec. IV-C leaf size).  far_s0 / far_smin set the deterministic far-field
+ * sample of each box's block row: the far boxes of the box's own level give
+ * far_s0 points each, one level up far_s0/2, ... never fewer than far_smin;
+ * far_s0 = 0 takes every far point (exact block row, small N only). */
+typedef struct {
+  double eta;          /* strong admissibility: far iff max(diam) <= eta*dist */
+  int32_t leaf;        /* maximum points per leaf box (<= 256) */
+  double tol;          /* relative rank tolerance of the pivoted QR / ID */
+  int32_t max_rank;    /* rank cap (<= 128) */
+  int32_t far_s0;      /* far-field sample per far box at the box's level */
+  int32_t far_smin;    /* minimum sample per far box */
+  int64_t hbm_budget_bytes; /* 0 = no budget check */
+} h2_options;
+
+/* Precision of the factorization.  The rank decisions (pivoted QR/ID), the
+ * redundant-block LU/Cholesky pivots and the refinement residual are FP64
+ * in every mode. */
+typedef enum { H2_FP64 = 0, H2_MIXED = 1 } h2_precision;
+
+typedef struct h2_handle_* h2_handle;
+
+/* Build the cluster tree (coordinate bisection), the strong-admissibility
+ * near/far lists and the H^2 operator used as the refinement residual:
+ * nested interpolative bases from the far-field block rows (eq. u,
+ * Sec. II-D: dense blocks never enter the basis) and the dense leaf near
+ * blocks.
+ *   points : N x 3 row-major doubles (host or device), caller order
+ *   N      : number of points, >= 1
+ *   kern   : kernel description (host pointer)
+ *   opt    : options (host pointer); leaf in [1,256], max_rank in [1,128],
+ *            tol >= 0, eta > 0
+ *   stream : cudaStream_t to issue work on (NULL = default stream)
+ *   out    : receives the handle
+ * Errors: H2_ERR_ARG, H2_ERR_NONFINITE (non-finite coordinate),
+ * H2_ERR_BUDGET, H2_ERR_OOM, H2_ERR_DEVICE. */
+h2_status h2_construct(const double* points, int64_t N, const h2_kernel* kern,
+                       const h2_options* opt, void* stream, h2_handle* out);
+
+/* Batched construct over P independent problems (each its own tree); the
+ * factor and solve then run every box of every problem at the same height
+ * above the leaves in one launch per step.
+ *   points[p] : N[p] x 3 row-major doubles of problem p
+ * Right-hand sides of a batched handle are stacked problem after problem
+ * (rows offset by the prefix sum of N). */
+h2_status h2_construct_batched(int32_t P, const double* const* points, const int64_t* N,
+                               const h2_kernel* kern, const h2_options* opt, void* stream,
+                               h2_handle* out);
+
+/* Dependency-free H^2-ULV factorization, level by level from the leaves
+ * (Sec. III-B fill-in pre-computation, Sec. III-C shared basis with
+ * fill-ins, eq. rs / eq. ss projection, eq. lu partial LU, merge, and the
+ * dense LU of eq. BLR2final at the top).
+ *   precision : H2_FP64 or H2_MIXED
+ *   spd       : nonzero = Cholesky instead of LU (symmetric positive
+ *               definite kernels only)
+ * Errors: H2_ERR_SINGULAR, H2_ERR_NOT_SPD, H2_ERR_OOM, H2_ERR_DEVICE. */
+h2_status h2_factor(h2_handle h, int32_t precision, int32_t spd);
+
+/* Solve A x = b with the ULV factors (Sec. II-B: L z = U^T b, U y = z,
+ * x = V^T y) and FP64 iterative refinement whose residual is the H^2
+ * matvec: x <- x + ULV^-1 (b - A_H2 x) until ||r|| / ||b|| <= target for
+ * every right-hand side or max_iter corrections were applied.
+ *   b, x   : N x nrhs column-major, leading dimension ld (host or device)
+ *   achieved_rel_residual : host array of nrhs (may be NULL)
+ *   iters  : host int, corrections applied (may be NULL)
+ * Errors: H2_ERR_STATE (not factored), H2_ERR_ARG, H2_ERR_NOT_CONVERGED
+ * (x still holds the last iterate). */
+h2_status h2_solve(h2_handle h, const double* b, double* x, int32_t nrhs, int64_t ld,
+                   double target_rel_residual, int32_t max_iter,
+                   double* achieved_rel_residual, int32_t* iters);
+
+/* y = A_H2 x, the H^2 operator used as the refinement residual (near blocks
+ * exact, far blocks through the nested bases, eq. transfer).
+ *   x, y : N x nrhs column-major, leading dimension ld (host or device) */
+h2_status h2_matvec(h2_handle h, const double* x, double* y, int32_t nrhs, int64_t ld);
+
+/* log|det A| and its sign from the factorization: the sum over every level
+ * and box of log|det S^RR_II| plus the root's (|det Q_I| = 1).  For a
+ * batched handle, problem p's value is written to log_abs_det[p] (host
+ * arrays of length P). */
+h2_status h2_logdet(h2_handle h, double* log_abs_det, int32_t* sign);
+
+/* JSON statistics: per-level ranks, flops, bytes, times (ms); cap = size of
+ * the host buffer json.  Truncated output is still NUL-terminated. */
+h2_status h2_stats(h2_handle h, char* json, size_t cap);
+
+/* Thread-local message of the last failed call on this thread. */
+const char* h2_last_error(void);
+
+/* Free every device buffer owned by the handle. */
+void h2_destroy(h2_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H2ULV_H */

@@ -1,0 +1,1707 @@
+// Host orchestration and C ABI of the H^2-ULV library.
+//
+// Level loop of the dependency-free H^2-ULV factorization (arXiv 2208.10907,
+// Sec. III): every step below is one batched launch over all boxes of all
+// problems at the same height above the leaves; there is no dependency
+// between boxes of a height, only between heights.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/h2ulv.h"
+#include "h2_common.cuh"
+#include "h2_tree.h"
+
+namespace h2 {
+
+// ------------------------------------------------------------------ memory --
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  explicit DBuf(size_t b) { alloc(b); }
+  void alloc(size_t b) {
+    release();
+    bytes = b;
+    if (b) {
+      cudaError_t e = cudaMalloc(&p, b);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        (void)cudaGetLastError();
+        throw StatusError(H2_ERR_OOM, "device allocation of " + std::to_string(b) + " bytes failed");
+      }
+    }
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  ~DBuf() { release(); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+using DBufP = std::shared_ptr<DBuf>;
+
+struct Scratch {
+  std::vector<DBufP> bufs;
+  cudaStream_t s;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  template <class T> T* up(const std::vector<T>& v) {
+    if (v.empty()) return nullptr;
+    auto b = std::make_shared<DBuf>(v.size() * sizeof(T));
+    H2_CUDA(cudaMemcpyAsync(b->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    bufs.push_back(b);
+    return b->template as<T>();
+  }
+  void* alloc(size_t bytes, bool zero = false) {
+    auto b = std::make_shared<DBuf>(std::max<size_t>(bytes, 16));
+    if (zero) H2_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, s));
+    bufs.push_back(b);
+    return b->p;
+  }
+};
+
+static size_t esz(Prec p) { return p == Prec::F64 ? 8 : 4; }
+
+// ---------------------------------------------------------- GEMM batches --
+struct GemmBatch {
+  std::vector<GemmTask> tasks;
+  std::vector<GemmTerm> terms;
+  int maxM = 0, maxN = 0;
+  void add(void* C, int ldc, int M, int N, double alpha, double beta, const void* Cin, int ldcin,
+           const std::vector<GemmTerm>& ts) {
+    if (M <= 0 || N <= 0) return;
+    GemmTask t;
+    t.C = C;
+    t.Cin = Cin;
+    t.M = M;
+    t.N = N;
+    t.ldc = ldc;
+    t.ldcin = ldcin;
+    t.t0 = (int)terms.size();
+    t.nt = 0;
+    for (const GemmTerm& g : ts)
+      if (g.K > 0) {
+        terms.push_back(g);
+        ++t.nt;
+      }
+    t.alpha = alpha;
+    t.beta = beta;
+    tasks.push_back(t);
+    maxM = std::max(maxM, M);
+    maxN = std::max(maxN, N);
+  }
+  void add1(void* C, int ldc, int M, int N, const void* A, int lda, const void* B, int ldb, int K,
+            double alpha = 1.0, double beta = 0.0, const void* Cin = nullptr, int ldcin = 0) {
+    add(C, ldc, M, N, alpha, beta, Cin ? Cin : (beta != 0.0 ? C : nullptr), Cin ? ldcin : ldc,
+        {GemmTerm{A, B, K, lda, ldb}});
+  }
+  void run(Prec p, bool trA, bool trB, Scratch& sc) {
+    if (tasks.empty()) return;
+    // the grid's y dimension is the tile count; chunk the task list so the
+    // x dimension stays well within limits
+    const size_t CH = 1u << 20;
+    for (size_t o = 0; o < tasks.size(); o += CH) {
+      size_t cnt = std::min(CH, tasks.size() - o);
+      std::vector<GemmTask> sub(tasks.begin() + o, tasks.begin() + o + cnt);
+      GemmTask* dt = sc.up(sub);
+      GemmTerm* dm = sc.up(terms);
+      launch_gemm(p, trA, trB, dt, dm, (int)cnt, maxM, maxN, sc.s);
+    }
+  }
+};
+
+// ------------------------------------------------------- handle structure --
+struct BoxRef {
+  int prob, level, local;
+};
+
+struct Height {
+  int nb = 0;                        // active boxes at this height
+  std::vector<BoxRef> ref;
+  std::vector<std::vector<int>> near, far;  // global ids at this height
+  std::vector<int> parent;           // global id at height+1, or -1 (root)
+  std::vector<int> root_slot;        // if parent == -1: index of the box in its problem's root
+  std::vector<int> first_child;      // global id of the first child at height-1 (H > 0)
+  // operator (H^2 matvec) basis
+  std::vector<int> n_op, r_op;
+  std::vector<std::vector<int>> cand_op, sk_op;   // global tree-order point ids
+  std::vector<DBufP> P_op;           // n_op x r_op interpolation (FP64)
+  std::vector<DBufP> Kfar_op;        // per far pair (flattened in near/far order)
+  std::vector<size_t> far_off;       // prefix of far pairs per box
+  std::vector<int64_t> xh_off;       // skeleton-vector offsets
+  int64_t xh_len = 0;
+  // ULV factor
+  std::vector<int> n, r;
+  std::vector<std::vector<int>> cand, sk;
+  DBufP Q;                           // per box n x n (FP64) [U^R U^S]
+  std::vector<size_t> q_off;         // element offsets into Q / S buffers (n^2 each)
+  DBufP Qw;                          // work-precision copy of Q (mixed mode)
+  DBufP S;                           // per box n x n FP64: LU of S^RR, U^RS, S^SR
+  DBufP Lt;                          // per box m x r FP64: (L^SR)^T
+  std::vector<size_t> lt_off;
+  DBufP pivRR;                       // per box m ints (offsets q_off-free: pv_off)
+  std::vector<size_t> pv_off;
+  DBufP W;                           // per box r x r FP64 (triangular factor of the ID)
+  std::vector<size_t> w_off;
+  std::vector<int64_t> v_off;        // level-vector offsets (solve)
+  int64_t v_len = 0;
+};
+
+struct Root {
+  int n = 0;
+  std::vector<int> off;              // offsets of the level-ltop boxes
+  DBufP A;                           // work-precision assembled matrix
+  DBufP LU;                          // FP64 LU factors
+  DBufP piv;
+  DBufP inv;                         // FP64 inverse
+  double logdet = 0.0, sign = 1.0;
+};
+
+struct Problem {
+  Tree t;
+  int64_t off = 0;                   // global tree-order offset
+  int H = 0;                         // number of ULV heights (L - ltop)
+  Root root;
+};
+
+struct Handle {
+  cudaStream_t s = nullptr;
+  KParams kp{};
+  h2_options opt{};
+  std::vector<Problem> probs;
+  int64_t Ntot = 0;
+  int Hmax = 0;
+  DBuf px, py, pz;                   // tree-order points
+  DBuf perm;                         // global tree position -> global caller row
+  std::vector<Height> hs;            // heights 0 .. Hmax-1 (plus leaf blocks)
+  // leaf near blocks (FP64), one per near pair at height 0 (also for H = 0
+  // problems, whose root is their whole leaf level)
+  std::vector<std::vector<int>> leaf_near;   // global leaf ids
+  std::vector<BoxRef> leaf_ref;
+  std::vector<size_t> leaf_blk_off;          // element offset per near pair
+  std::vector<size_t> leaf_pair_ptr;         // CSR row pointer over leaves
+  DBuf leaf_blk;
+  std::vector<int> leaf_n;
+  std::vector<int64_t> leaf_s;               // global tree-order start per leaf
+  bool factored = false;
+  int precision = 0, spd = 0;
+  double t_construct_ms = 0, t_factor_ms = 0;
+  std::vector<double> level_ms;
+  std::string stats_extra;
+};
+
+static Points points(const Handle& h) {
+  return Points{h.px.as<double>(), h.py.as<double>(), h.pz.as<double>()};
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------- construct --
+static void build_heights(Handle& h) {
+  // leaves (height 0) of every problem, including problems with H = 0
+  int nleaf = 0;
+  std::vector<int> leaf_base(h.probs.size());
+  for (size_t p = 0; p < h.probs.size(); ++p) {
+    leaf_base[p] = nleaf;
+    nleaf += (int)h.probs[p].t.boxes[h.probs[p].t.L].size();
+  }
+  h.leaf_ref.resize(nleaf);
+  h.leaf_near.resize(nleaf);
+  h.leaf_n.resize(nleaf);
+  h.leaf_s.resize(nleaf);
+  for (size_t p = 0; p < h.probs.size(); ++p) {
+    const Tree& t = h.probs[p].t;
+    for (size_t i = 0; i < t.boxes[t.L].size(); ++i) {
+      int g = leaf_base[p] + (int)i;
+      h.leaf_ref[g] = BoxRef{(int)p, t.L, (int)i};
+      for (int j : t.near[t.L][i]) h.leaf_near[g].push_back(leaf_base[p] + j);
+      h.leaf_n[g] = (int)(t.boxes[t.L][i].e - t.boxes[t.L][i].s);
+      h.leaf_s[g] = h.probs[p].off + t.boxes[t.L][i].s;
+    }
+  }
+  // ULV / operator heights
+  h.Hmax = 0;
+  for (auto& pb : h.probs) h.Hmax = std::max(h.Hmax, pb.H);
+  h.hs.assign(h.Hmax, Height());
+  std::vector<std::vector<int>> base(h.Hmax, std::vector<int>(h.probs.size(), -1));
+  for (int H = 0; H < h.Hmax; ++H) {
+    Height& ht = h.hs[H];
+    int nb = 0;
+    for (size_t p = 0; p < h.probs.size(); ++p) {
+      const Problem& pb = h.probs[p];
+      if (H < pb.H) {
+        base[H][p] = nb;
+        nb += (int)pb.t.boxes[pb.t.L - H].size();
+      }
+    }
+    ht.nb = nb;
+    ht.ref.resize(nb);
+    ht.near.resize(nb);
+    ht.far.resize(nb);
+    ht.parent.assign(nb, -1);
+    ht.root_slot.assign(nb, -1);
+    ht.first_child.assign(nb, -1);
+  }
+  for (int H = 0; H < h.Hmax; ++H) {
+    Height& ht = h.hs[H];
+    for (size_t p = 0; p < h.probs.size(); ++p) {
+      const Problem& pb = h.probs[p];
+      if (H >= pb.H) continue;
+      int l = pb.t.L - H;
+      for (size_t i = 0; i < pb.t.boxes[l].size(); ++i) {
+        int g = base[H][p] + (int)i;
+        ht.ref[g] = BoxRef{(int)p, l, (int)i};
+        for (int j : pb.t.near[l][i]) ht.near[g].push_back(base[H][p] + j);
+        for (int j : pb.t.far[l][i]) ht.far[g].push_back(base[H][p] + j);
+        if (H + 1 < pb.H) ht.parent[g] = base[H + 1][p] + (int)i / 2;
+        else ht.root_slot[g] = (int)i / 2;
+        if (H > 0) ht.first_child[g] = base[H - 1][p] + 2 * (int)i;
+      }
+    }
+  }
+}
+
+// The H^2 operator: per height, nested interpolative bases from the sampled
+// far-field block rows (eq. u with the low-rank blocks only), the far
+// skeleton blocks K(sk_I, sk_J) and the dense leaf near blocks.
+static void build_operator(Handle& h) {
+  cudaStream_t s = h.s;
+  Points pts = points(h);
+  // leaf near blocks (FP64)
+  int nleaf = (int)h.leaf_ref.size();
+  h.leaf_pair_ptr.assign(nleaf + 1, 0);
+  for (int g = 0; g < nleaf; ++g) h.leaf_pair_ptr[g + 1] = h.leaf_pair_ptr[g] + h.leaf_near[g].size();
+  h.leaf_blk_off.resize(h.leaf_pair_ptr[nleaf] + 1);
+  size_t tot = 0;
+  for (int g = 0; g < nleaf; ++g)
+    for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
+      h.leaf_blk_off[h.leaf_pair_ptr[g] + q] = tot;
+      tot += (size_t)h.leaf_n[g] * h.leaf_n[h.leaf_near[g][q]];
+    }
+  h.leaf_blk_off[h.leaf_pair_ptr[nleaf]] = tot;
+  if (h.opt.hbm_budget_bytes > 0 && (int64_t)(tot * 8) > h.opt.hbm_budget_bytes)
+    throw StatusError(H2_ERR_BUDGET, "leaf near blocks alone need " + std::to_string(tot * 8) + " bytes");
+  h.leaf_blk.alloc(tot * 8);
+  {
+    Scratch sc(s);
+    std::vector<AsmTask> tasks;
+    int maxc = 0;
+    for (int g = 0; g < nleaf; ++g)
+      for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
+        int j = h.leaf_near[g][q];
+        AsmTask a;
+        a.out = h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[g] + q];
+        a.ridx = nullptr;
+        a.cidx = nullptr;
+        a.r0 = (int)h.leaf_s[g];
+        a.c0 = (int)h.leaf_s[j];
+        a.nr = h.leaf_n[g];
+        a.nc = h.leaf_n[j];
+        a.ld = h.leaf_n[g];
+        tasks.push_back(a);
+        maxc = std::max(maxc, a.nc);
+      }
+    for (size_t o = 0; o < tasks.size(); o += (1u << 20)) {
+      std::vector<AsmTask> sub(tasks.begin() + o, tasks.begin() + std::min(tasks.size(), o + (1u << 20)));
+      launch_assemble(Prec::F64, sc.up(sub), (int)sub.size(), 256, maxc, pts, h.kp, s);
+    }
+    H2_CUDA(cudaStreamSynchronize(s));
+  }
+  // operator bases, height by height
+  std::vector<int64_t> samp;
+  for (int H = 0; H < h.Hmax; ++H) {
+    Height& ht = h.hs[H];
+    Scratch sc(s);
+    ht.n_op.resize(ht.nb);
+    ht.r_op.resize(ht.nb);
+    ht.cand_op.resize(ht.nb);
+    ht.sk_op.resize(ht.nb);
+    for (int g = 0; g < ht.nb; ++g) {
+      const BoxRef& b = ht.ref[g];
+      const Problem& pb = h.probs[b.prob];
+      if (H == 0) {
+        const Box& bx = pb.t.boxes[b.level][b.local];
+        ht.cand_op[g].resize(bx.e - bx.s);
+        for (int64_t q = bx.s; q < bx.e; ++q) ht.cand_op[g][q - bx.s] = (int)(pb.off + q);
+      }
+      ht.n_op[g] = (int)ht.cand_op[g].size();
+    }
+    // samples and fold
+    std::vector<int> samp_all;
+    std::vector<size_t> samp_off(ht.nb + 1, 0);
+    std::vector<int> cand_all;
+    std::vector<size_t> cand_off(ht.nb + 1, 0);
+    for (int g = 0; g < ht.nb; ++g) {
+      const BoxRef& b = ht.ref[g];
+      const Problem& pb = h.probs[b.prob];
+      far_samples(pb.t, b.level, b.local, h.opt.far_s0, h.opt.far_smin, samp);
+      for (int64_t q : samp) samp_all.push_back((int)(pb.off + q));
+      samp_off[g + 1] = samp_all.size();
+      cand_all.insert(cand_all.end(), ht.cand_op[g].begin(), ht.cand_op[g].end());
+      cand_off[g + 1] = cand_all.size();
+    }
+    int* d_samp = sc.up(samp_all);
+    int* d_cand = sc.up(cand_all);
+    size_t rtot = 0;
+    std::vector<size_t> r_off(ht.nb + 1, 0);
+    for (int g = 0; g < ht.nb; ++g) r_off[g + 1] = r_off[g] + (size_t)ht.n_op[g] * ht.n_op[g];
+    double* R0 = (double*)sc.alloc(r_off[ht.nb] * 8, true);
+    double* Rq = (double*)sc.alloc(r_off[ht.nb] * 8, true);
+    int* piv = (int*)sc.alloc(cand_off[ht.nb] * 4);
+    int* rank = (int*)sc.alloc(ht.nb * 4);
+    std::vector<FoldTask> ft;
+    std::vector<PqrTask> qt;
+    std::vector<int> has_far(ht.nb, 0);
+    for (int g = 0; g < ht.nb; ++g) {
+      int n = ht.n_op[g];
+      int m = (int)(samp_off[g + 1] - samp_off[g]);
+      if (m == 0 || n == 0) continue;
+      has_far[g] = 1;
+      ft.push_back(FoldTask{d_cand + cand_off[g], d_samp + samp_off[g], R0 + r_off[g], n, m});
+      qt.push_back(PqrTask{R0 + r_off[g], n, n, n, piv + cand_off[g], Rq + r_off[g], rank + g, h.opt.tol,
+                           h.opt.max_rank});
+    }
+    launch_fold(sc.up(ft), (int)ft.size(), pts, h.kp, s);
+    launch_pqr(sc.up(qt), (int)qt.size(), s);
+    std::vector<int> hr(ht.nb), hpiv(cand_off[ht.nb]);
+    H2_CUDA(cudaMemcpyAsync(hr.data(), rank, ht.nb * 4, cudaMemcpyDeviceToHost, s));
+    if (!hpiv.empty())
+      H2_CUDA(cudaMemcpyAsync(hpiv.data(), piv, hpiv.size() * 4, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    // ID: T = R11^-1 R12, P = interpolation matrix; sk = cand[piv[:r]]
+    std::vector<TrsmTask> tt;
+    std::vector<InterpTask> it;
+    ht.P_op.resize(ht.nb);
+    int maxrhs = 0;
+    for (int g = 0; g < ht.nb; ++g) {
+      int n = ht.n_op[g];
+      int r = has_far[g] ? hr[g] : n;
+      if (r == 0) r = n;   // empty far field or zero block row: keep every point
+      bool keep_all = (!has_far[g]) || hr[g] == 0;
+      ht.r_op[g] = r;
+      ht.P_op[g] = std::make_shared<DBuf>((size_t)std::max(1, n * r) * 8);
+      ht.sk_op[g].resize(r);
+      if (keep_all) {
+        for (int q = 0; q < r; ++q) ht.sk_op[g][q] = ht.cand_op[g][q];
+        launch_fill_eye(Prec::F64, ht.P_op[g]->p, n, n, s);
+        continue;
+      }
+      for (int q = 0; q < r; ++q) ht.sk_op[g][q] = ht.cand_op[g][hpiv[cand_off[g] + q]];
+      if (r < n) {
+        tt.push_back(TrsmTask{Rq + r_off[g], Rq + r_off[g] + (size_t)r * n, r, n - r, n, n, nullptr});
+        maxrhs = std::max(maxrhs, n - r);
+      }
+      it.push_back(InterpTask{piv + cand_off[g], Rq + r_off[g] + (size_t)r * n, ht.P_op[g]->p, n, r, n});
+    }
+    launch_trsm(Prec::F64, false, false, false, sc.up(tt), (int)tt.size(), maxrhs, s);
+    launch_interp(Prec::F64, sc.up(it), (int)it.size(), s);
+    // far skeleton blocks K(sk_I, sk_J)
+    ht.far_off.assign(ht.nb + 1, 0);
+    for (int g = 0; g < ht.nb; ++g) ht.far_off[g + 1] = ht.far_off[g] + ht.far[g].size();
+    std::vector<int> sk_all;
+    std::vector<size_t> sk_off(ht.nb + 1, 0);
+    for (int g = 0; g < ht.nb; ++g) {
+      sk_all.insert(sk_all.end(), ht.sk_op[g].begin(), ht.sk_op[g].end());
+      sk_off[g + 1] = sk_all.size();
+    }
+    int* d_sk = sc.up(sk_all);
+    ht.Kfar_op.resize(ht.far_off[ht.nb]);
+    std::vector<AsmTask> at;
+    int maxc = 0;
+    for (int g = 0; g < ht.nb; ++g)
+      for (size_t q = 0; q < ht.far[g].size(); ++q) {
+        int j = ht.far[g][q];
+        auto blk = std::make_shared<DBuf>((size_t)ht.r_op[g] * ht.r_op[j] * 8);
+        ht.Kfar_op[ht.far_off[g] + q] = blk;
+        at.push_back(AsmTask{blk->p, d_sk + sk_off[g], d_sk + sk_off[j], 0, 0, ht.r_op[g], ht.r_op[j], ht.r_op[g]});
+        maxc = std::max(maxc, ht.r_op[j]);
+      }
+    launch_assemble(Prec::F64, sc.up(at), (int)at.size(), 256, maxc, pts, h.kp, s);
+    // skeleton-vector offsets
+    ht.xh_off.assign(ht.nb + 1, 0);
+    for (int g = 0; g < ht.nb; ++g) ht.xh_off[g + 1] = ht.xh_off[g] + ht.r_op[g];
+    ht.xh_len = ht.xh_off[ht.nb];
+    // next height's candidates
+    if (H + 1 < h.Hmax) {
+      Height& up = h.hs[H + 1];
+      up.cand_op.resize(up.nb);
+      for (int g = 0; g < ht.nb; ++g) {
+        int pg = ht.parent[g];
+        if (pg < 0) continue;
+        auto& c = up.cand_op[pg];
+        c.insert(c.end(), ht.sk_op[g].begin(), ht.sk_op[g].end());
+      }
+    }
+    H2_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+// ------------------------------------------------------------- matvec ----
+// y = A_H2 x in tree order (N x nrhs, column-major, ld = Ntot).
+static void matvec_tree(Handle& h, const double* x, double* y, int nrhs) {
+  cudaStream_t s = h.s;
+  Scratch sc(s);
+  const int64_t ld = h.Ntot;
+  // near part (leaf dense blocks): y_I = sum_J A_IJ x_J
+  {
+    GemmBatch gb;
+    for (size_t g = 0; g < h.leaf_ref.size(); ++g) {
+      std::vector<GemmTerm> ts;
+      for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
+        int j = h.leaf_near[g][q];
+        ts.push_back(GemmTerm{h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[g] + q],
+                              x + h.leaf_s[j], h.leaf_n[j], h.leaf_n[g], (int)ld});
+      }
+      gb.add(y + h.leaf_s[g], (int)ld, h.leaf_n[g], nrhs, 1.0, 0.0, nullptr, 0, ts);
+    }
+    gb.run(Prec::F64, false, false, sc);
+  }
+  if (h.Hmax == 0) return;
+  // upward pass
+  std::vector<double*> xh(h.Hmax), yh(h.Hmax);
+  for (int H = 0; H < h.Hmax; ++H) {
+    xh[H] = (double*)sc.alloc((size_t)h.hs[H].xh_len * nrhs * 8);
+    yh[H] = (double*)sc.alloc((size_t)h.hs[H].xh_len * nrhs * 8, true);
+  }
+  for (int H = 0; H < h.Hmax; ++H) {
+    Height& ht = h.hs[H];
+    GemmBatch gb;
+    for (int g = 0; g < ht.nb; ++g) {
+      const double* src;
+      int64_t lds;
+      if (H == 0) {
+        const BoxRef& b = ht.ref[g];
+        const Problem& pb = h.probs[b.prob];
+        src = x + pb.off + pb.t.boxes[b.level][b.local].s;
+        lds = ld;
+      } else {
+        // children a, b are adjacent in the skeleton vector of height H-1
+        const Height& dn = h.hs[H - 1];
+        int a = ht.first_child[g];
+        src = xh[H - 1] + dn.xh_off[a];
+        lds = dn.xh_len;
+      }
+      gb.add1(xh[H] + ht.xh_off[g], (int)ht.xh_len, ht.r_op[g], nrhs, ht.P_op[g]->p, ht.n_op[g], src, (int)lds,
+              ht.n_op[g]);
+    }
+    gb.run(Prec::F64, true, false, sc);
+  }
+  // far interactions at every height
+  for (int H = 0; H < h.Hmax; ++H) {
+    Height& ht = h.hs[H];
+    GemmBatch gb;
+    for (int g = 0; g < ht.nb; ++g) {
+      std::vector<GemmTerm> ts;
+      for (size_t q = 0; q < ht.far[g].size(); ++q) {
+        int j = ht.far[g][q];
+        ts.push_back(GemmTerm{ht.Kfar_op[ht.far_off[g] + q]->p, xh[H] + ht.xh_off[j], ht.r_op[j], ht.r_op[g],
+                              (int)ht.xh_len});
+      }
+      if (!ts.empty()) gb.add(yh[H] + ht.xh_off[g], (int)ht.xh_len, ht.r_op[g], nrhs, 1.0, 0.0, nullptr, 0, ts);
+    }
+    gb.run(Prec::F64, false, false, sc);
+  }
+  // downward pass: yh(children) += P_P yh(P)
+  for (int H = h.Hmax - 1; H >= 1; --H) {
+    Height& ht = h.hs[H];
+    const Height& dn = h.hs[H - 1];
+    GemmBatch gb;
+    for (int g = 0; g < ht.nb; ++g) {
+      int a = ht.first_child[g];
+      double* dst = yh[H - 1] + dn.xh_off[a];
+      gb.add1(dst, (int)dn.xh_len, ht.n_op[g], nrhs, ht.P_op[g]->p, ht.n_op[g], yh[H] + ht.xh_off[g],
+              (int)ht.xh_len, ht.r_op[g], 1.0, 1.0);
+    }
+    gb.run(Prec::F64, false, false, sc);
+  }
+  // leaf: y_I += P_I yh(I)
+  {
+    Height& ht = h.hs[0];
+    GemmBatch gb;
+    for (int g = 0; g < ht.nb; ++g) {
+      const BoxRef& b = ht.ref[g];
+      const Problem& pb = h.probs[b.prob];
+      double* dst = y + pb.off + pb.t.boxes[b.level][b.local].s;
+      gb.add1(dst, (int)ld, ht.n_op[g], nrhs, ht.P_op[g]->p, ht.n_op[g], yh[0] + ht.xh_off[g], (int)ht.xh_len,
+              ht.r_op[g], 1.0, 1.0);
+    }
+    gb.run(Prec::F64, false, false, sc);
+  }
+  H2_CUDA(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------ root LU ----
+// Blocked right-looking LU with partial pivoting of the dense top-level
+// matrix (eq. BLR2final), then its inverse (the root solve becomes a GEMM).
+static void root_factor(Handle& h, Root& rt, int spd) {
+  (void)spd;
+  cudaStream_t s = h.s;
+  const int n = rt.n;
+  if (n == 0) return;
+  if (n > 8192) throw StatusError(H2_ERR_ARG, "top-level dense matrix larger than 8192");
+  Scratch sc(s);
+  double* A = rt.LU->as<double>();
+  int* piv = rt.piv->as<int>();
+  int* info = (int*)sc.alloc(4, true);
+  const int NB = 64;
+  for (int k = 0; k < n; k += NB) {
+    int nb = std::min(NB, n - k);
+    std::vector<LuTask> lt{LuTask{A + k + (size_t)k * n, n - k, nb, n, piv + k, info}};
+    launch_getrf(Prec::F64, sc.up(lt), 1, s);
+    // pivots are panel-relative: convert to global rows and apply to the
+    // columns left and right of the panel
+    std::vector<CopyTask> none;
+    // relative -> absolute pivots on the device via a tiny GEMM-free kernel:
+    // done on the host for simplicity (nb ints)
+    std::vector<int> hp(nb);
+    H2_CUDA(cudaMemcpyAsync(hp.data(), piv + k, nb * 4, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    for (int& v : hp) v += k;
+    H2_CUDA(cudaMemcpyAsync(piv + k, hp.data(), nb * 4, cudaMemcpyHostToDevice, s));
+    launch_laswp_cols(Prec::F64, A, n, n, piv, k, k + nb, 0, k, s);
+    launch_laswp_cols(Prec::F64, A, n, n, piv, k, k + nb, k + nb, n, s);
+    if (k + nb < n) {
+      // U12 = L11^-1 A12
+      std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, A + k + (size_t)(k + nb) * n, nb, n - k - nb, n, n,
+                                        nullptr}};
+      launch_trsm(Prec::F64, true, true, false, sc.up(tt), 1, n - k - nb, s);
+      // A22 -= L21 U12
+      GemmBatch gb;
+      gb.add1(A + (k + nb) + (size_t)(k + nb) * n, n, n - k - nb, n - k - nb, A + (k + nb) + (size_t)k * n, n,
+              A + k + (size_t)(k + nb) * n, n, nb, -1.0, 1.0);
+      gb.run(Prec::F64, false, false, sc);
+    }
+  }
+  int hinfo = 0;
+  H2_CUDA(cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, s));
+  H2_CUDA(cudaStreamSynchronize(s));
+  if (hinfo != 0) throw StatusError(H2_ERR_SINGULAR, "zero pivot in the top-level LU");
+  // log-determinant
+  {
+    std::vector<LuTask> lt{LuTask{A, n, n, n, piv, nullptr}};
+    double* o = (double*)sc.alloc(16);
+    launch_logdet_lu(sc.up(lt), 1, o, o + 1, false, s);
+    double ho[2];
+    H2_CUDA(cudaMemcpyAsync(ho, o, 16, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    rt.logdet = ho[0];
+    rt.sign = ho[1];
+  }
+  // inverse: X = U^-1 L^-1 P I, blocked by 256-row panels
+  rt.inv = std::make_shared<DBuf>((size_t)n * n * 8);
+  double* X = rt.inv->as<double>();
+  launch_fill_eye(Prec::F64, X, n, n, s);
+  launch_laswp_cols(Prec::F64, X, n, n, piv, 0, n, 0, n, s);
+  const int TB = 256;
+  // forward: L (unit lower)
+  for (int k = 0; k < n; k += TB) {
+    int nb = std::min(TB, n - k);
+    std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, X + k, nb, n, n, n, nullptr}};
+    launch_trsm(Prec::F64, true, true, false, sc.up(tt), 1, n, s);
+    if (k + nb < n) {
+      GemmBatch gb;
+      gb.add1(X + k + nb, n, n - k - nb, n, A + (k + nb) + (size_t)k * n, n, X + k, n, nb, -1.0, 1.0);
+      gb.run(Prec::F64, false, false, sc);
+    }
+  }
+  // backward: U (upper)
+  for (int k = ((n - 1) / TB) * TB; k >= 0; k -= TB) {
+    int nb = std::min(TB, n - k);
+    std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, X + k, nb, n, n, n, nullptr}};
+    launch_trsm(Prec::F64, false, false, false, sc.up(tt), 1, n, s);
+    if (k > 0) {
+      GemmBatch gb;
+      gb.add1(X, n, k, n, A + (size_t)k * n, n, X + k, n, nb, -1.0, 1.0);
+      gb.run(Prec::F64, false, false, sc);
+    }
+  }
+  H2_CUDA(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------- factor ----
+struct PairRef {
+  void* ptr;   // block pointer (work precision)
+  int ld;
+};
+
+static void factor(Handle& h, int precision, int spd) {
+  cudaStream_t s = h.s;
+  const Prec W = precision == H2_MIXED ? Prec::F32 : Prec::F64;
+  const size_t ws = esz(W);
+  Points pts = points(h);
+  h.level_ms.clear();
+  // near blocks of the current height, in work precision: A[g][q] for the
+  // q-th near box of g
+  std::vector<std::vector<PairRef>> Ablk;
+  std::vector<DBufP> Aown;       // storage owned for the current height
+  // height-0 inputs: the FP64 leaf near blocks (converted in mixed mode)
+  std::vector<int> ncur;
+  for (auto& pb : h.probs) {
+    pb.root = Root();
+  }
+  // problems with no ULV height: root = their leaf level (all pairs near)
+  auto setup_root = [&](Problem& pb, const std::vector<int>& sizes) {
+    Root& rt = pb.root;
+    rt.off.assign(sizes.size() + 1, 0);
+    for (size_t i = 0; i < sizes.size(); ++i) rt.off[i + 1] = rt.off[i] + sizes[i];
+    rt.n = rt.off.back();
+    if (rt.n > 8192) throw StatusError(H2_ERR_ARG, "top-level dense matrix larger than 8192");
+    rt.A = std::make_shared<DBuf>((size_t)rt.n * rt.n * ws);
+    H2_CUDA(cudaMemsetAsync(rt.A->p, 0, rt.A->bytes, s));
+    rt.LU = std::make_shared<DBuf>((size_t)rt.n * rt.n * 8);
+    rt.piv = std::make_shared<DBuf>((size_t)rt.n * 4);
+  };
+  {
+    Scratch sc(s);
+    for (size_t p = 0; p < h.probs.size(); ++p) {
+      Problem& pb = h.probs[p];
+      if (pb.H > 0) continue;
+      std::vector<int> sizes;
+      for (auto& bx : pb.t.boxes[pb.t.L]) sizes.push_back((int)(bx.e - bx.s));
+      setup_root(pb, sizes);
+      // copy the leaf blocks into the root matrix
+      std::vector<CopyTask> ct;
+      int maxr = 0, maxc = 0;
+      for (size_t g = 0; g < h.leaf_ref.size(); ++g) {
+        if (h.leaf_ref[g].prob != (int)p) continue;
+        int i = h.leaf_ref[g].local;
+        for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
+          int jg = h.leaf_near[g][q];
+          int j = h.leaf_ref[jg].local;
+          ct.push_back(CopyTask{h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[g] + q],
+                                (char*)pb.root.A->p + ((size_t)pb.root.off[i] + (size_t)pb.root.off[j] * pb.root.n) * ws,
+                                h.leaf_n[g], h.leaf_n[jg], h.leaf_n[g], pb.root.n});
+          maxr = std::max(maxr, h.leaf_n[g]);
+          maxc = std::max(maxc, h.leaf_n[jg]);
+        }
+      }
+      launch_copy(Prec::F64, W, false, sc.up(ct), (int)ct.size(), maxr, maxc, s);
+    }
+    H2_CUDA(cudaStreamSynchronize(s));
+  }
+  if (h.Hmax > 0) {
+    Height& h0 = h.hs[0];
+    Ablk.assign(h0.nb, {});
+    // map height-0 ids to leaf ids
+    std::vector<int> leaf_of(h0.nb);
+    {
+      std::map<std::pair<int, int>, int> lid;
+      for (size_t g = 0; g < h.leaf_ref.size(); ++g) lid[{h.leaf_ref[g].prob, h.leaf_ref[g].local}] = (int)g;
+      for (int g = 0; g < h0.nb; ++g) leaf_of[g] = lid[{h0.ref[g].prob, h0.ref[g].local}];
+    }
+    if (W == Prec::F64) {
+      for (int g = 0; g < h0.nb; ++g) {
+        int lg = leaf_of[g];
+        for (size_t q = 0; q < h0.near[g].size(); ++q)
+          Ablk[g].push_back(PairRef{h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[lg] + q], h.leaf_n[lg]});
+      }
+    } else {
+      // FP32 copy of the leaf near blocks for the mixed-precision pass
+      size_t tot = 0;
+      for (int g = 0; g < h0.nb; ++g) {
+        int lg = leaf_of[g];
+        tot += h.leaf_blk_off[h.leaf_pair_ptr[lg + 1]] - h.leaf_blk_off[h.leaf_pair_ptr[lg]];
+      }
+      auto buf = std::make_shared<DBuf>(tot * 4);
+      Aown.push_back(buf);
+      Scratch sc(s);
+      std::vector<CopyTask> ct;
+      size_t o = 0;
+      int maxr = 0, maxc = 0;
+      for (int g = 0; g < h0.nb; ++g) {
+        int lg = leaf_of[g];
+        for (size_t q = 0; q < h0.near[g].size(); ++q) {
+          int jg = leaf_of[h0.near[g][q]];
+          size_t cnt = (size_t)h.leaf_n[lg] * h.leaf_n[jg];
+          float* dst = buf->as<float>() + o;
+          ct.push_back(CopyTask{h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[lg] + q], dst, h.leaf_n[lg],
+                                h.leaf_n[jg], h.leaf_n[lg], h.leaf_n[lg]});
+          Ablk[g].push_back(PairRef{dst, h.leaf_n[lg]});
+          o += cnt;
+          maxr = std::max(maxr, h.leaf_n[lg]);
+          maxc = std::max(maxc, h.leaf_n[jg]);
+        }
+      }
+      launch_copy(Prec::F64, Prec::F32, false, sc.up(ct), (int)ct.size(), maxr, maxc, s);
+      H2_CUDA(cudaStreamSynchronize(s));
+    }
+    h0.n.resize(h0.nb);
+    h0.cand.resize(h0.nb);
+    for (int g = 0; g < h0.nb; ++g) {
+      h0.n[g] = h.leaf_n[leaf_of[g]];
+      h0.cand[g].resize(h0.n[g]);
+      for (int q = 0; q < h0.n[g]; ++q) h0.cand[g][q] = (int)(h.leaf_s[leaf_of[g]] + q);
+    }
+  }
+  DBufP Tcur;                       // per box n x n FP64 transforms (H > 0)
+  std::vector<size_t> t_off;
+  std::vector<int64_t> samp;
+  for (int H = 0; H < h.Hmax; ++H) {
+    double t0 = now_ms();
+    Height& ht = h.hs[H];
+    Scratch sc(s);
+    const int nb = ht.nb;
+    std::vector<int>& n = ht.n;
+    // n x n slots
+    std::vector<size_t> off(nb + 1, 0);
+    for (int g = 0; g < nb; ++g) off[g + 1] = off[g] + (size_t)n[g] * n[g];
+    const size_t NN = off[nb];
+    int maxn = 0;
+    for (int g = 0; g < nb; ++g) maxn = std::max(maxn, n[g]);
+    auto diag_q = [&](int g) -> int {
+      for (size_t q = 0; q < ht.near[g].size(); ++q)
+        if (ht.near[g][q] == g) return (int)q;
+      return -1;
+    };
+    // ---------------- 1. fill-ins (Sec. III-B) --------------------------
+    std::vector<int> has_lu(nb, 0);
+    for (int g = 0; g < nb; ++g) has_lu[g] = ht.near[g].size() > 1;
+    // scratch slots of maxn x maxn per box (V blocks are n_I x n_K)
+    const size_t SL = (size_t)maxn * maxn;
+    std::vector<size_t> so(nb + 1, 0);
+    for (int g = 0; g <= nb; ++g) so[g] = (size_t)g * SL;
+    void* LUK = sc.alloc(so[nb] * ws);
+    int* pivK = (int*)sc.alloc((size_t)nb * 256 * 4);
+    void* Mk = sc.alloc(so[nb] * ws, true);
+    void* Tmp = sc.alloc(so[nb] * ws);
+    {
+      std::vector<CopyTask> ct;
+      std::vector<LuTask> lu;
+      GemmBatch ng;
+      for (int g = 0; g < nb; ++g) {
+        if (!has_lu[g]) continue;
+        int dq = diag_q(g);
+        void* dst = (char*)LUK + so[g] * ws;
+        ct.push_back(CopyTask{Ablk[g][dq].ptr, dst, n[g], n[g], Ablk[g][dq].ld, n[g]});
+        lu.push_back(LuTask{dst, n[g], n[g], n[g], pivK + (size_t)g * 256, nullptr});
+        std::vector<GemmTerm> ts;
+        for (size_t q = 0; q < ht.near[g].size(); ++q) {
+          int j = ht.near[g][q];
+          if (j == g) continue;
+          ts.push_back(GemmTerm{Ablk[g][q].ptr, Ablk[g][q].ptr, n[j], Ablk[g][q].ld, Ablk[g][q].ld});
+        }
+        ng.add((char*)Mk + so[g] * ws, n[g], n[g], n[g], 1.0, 0.0, nullptr, 0, ts);
+      }
+      launch_copy(W, W, false, sc.up(ct), (int)ct.size(), maxn, maxn, s);
+      launch_getrf(W, sc.up(lu), (int)lu.size(), s);
+      ng.run(W, false, true, sc);
+      // M_K = A_KK^-1 NG_K A_KK^-T  (NG symmetric): X = A^-1 NG; M = A^-1 X^T
+      std::vector<TrsmTask> tl, tu;
+      std::vector<CopyTask> tr;
+      for (int g = 0; g < nb; ++g) {
+        if (!has_lu[g]) continue;
+        void* L = (char*)LUK + so[g] * ws;
+        void* M = (char*)Mk + so[g] * ws;
+        tl.push_back(TrsmTask{L, M, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
+        tu.push_back(TrsmTask{L, M, n[g], n[g], n[g], n[g], nullptr});
+        tr.push_back(CopyTask{M, (char*)Tmp + so[g] * ws, n[g], n[g], n[g], n[g]});
+      }
+      TrsmTask* dtl = sc.up(tl);
+      TrsmTask* dtu = sc.up(tu);
+      launch_trsm(W, true, true, false, dtl, (int)tl.size(), maxn, s);
+      launch_trsm(W, false, false, false, dtu, (int)tu.size(), maxn, s);
+      launch_copy(W, W, true, sc.up(tr), (int)tr.size(), maxn, maxn, s);
+      std::vector<TrsmTask> tl2, tu2;
+      for (int g = 0; g < nb; ++g) {
+        if (!has_lu[g]) continue;
+        void* L = (char*)LUK + so[g] * ws;
+        void* X = (char*)Tmp + so[g] * ws;
+        tl2.push_back(TrsmTask{L, X, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
+        tu2.push_back(TrsmTask{L, X, n[g], n[g], n[g], n[g], nullptr});
+      }
+      launch_trsm(W, true, true, false, sc.up(tl2), (int)tl2.size(), maxn, s);
+      launch_trsm(W, false, false, false, sc.up(tu2), (int)tu2.size(), maxn, s);
+      // M = Tmp (symmetric up to rounding)
+      std::swap(Mk, Tmp);
+    }
+    // Gram of the fill-in block row: sum_K A_IK M_K A_IK^T, by near position
+    void* GF = sc.alloc(so[nb] * ws, true);
+    {
+      size_t maxdeg = 0;
+      for (int g = 0; g < nb; ++g) maxdeg = std::max(maxdeg, ht.near[g].size());
+      for (size_t k = 0; k < maxdeg; ++k) {
+        GemmBatch g1, g2;
+        for (int g = 0; g < nb; ++g) {
+          if (k >= ht.near[g].size()) continue;
+          int K = ht.near[g][k];
+          if (K == g || !has_lu[K]) continue;
+          void* V = (char*)Tmp + so[g] * ws;
+          g1.add1(V, n[g], n[g], n[K], Ablk[g][k].ptr, Ablk[g][k].ld, (char*)Mk + so[K] * ws, n[K], n[K]);
+          g2.add1((char*)GF + so[g] * ws, n[g], n[g], n[g], V, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K], 1.0, 1.0);
+        }
+        g1.run(W, false, false, sc);
+        g2.run(W, false, true, sc);
+      }
+    }
+    // ---------------- 2. basis with fill-ins (eq. fillu) ---------------
+    double* G = (double*)sc.alloc(NN * 8);
+    {
+      std::vector<CopyTask> ct;
+      for (int g = 0; g < nb; ++g) ct.push_back(CopyTask{(char*)GF + so[g] * ws, G + off[g], n[g], n[g], n[g], n[g]});
+      launch_copy(W, Prec::F64, false, sc.up(ct), (int)ct.size(), maxn, maxn, s);
+      if (H > 0) {
+        // point form: T^-1 G T^-T (T = blockdiag(W_a, W_b), upper triangular)
+        double* G2 = (double*)sc.alloc(NN * 8);
+        std::vector<TrsmTask> t1, t2;
+        std::vector<CopyTask> tr;
+        for (int g = 0; g < nb; ++g) {
+          t1.push_back(TrsmTask{Tcur->as<double>() + t_off[g], G + off[g], n[g], n[g], n[g], n[g], nullptr});
+          tr.push_back(CopyTask{G + off[g], G2 + off[g], n[g], n[g], n[g], n[g]});
+          t2.push_back(TrsmTask{Tcur->as<double>() + t_off[g], G2 + off[g], n[g], n[g], n[g], n[g], nullptr});
+        }
+        launch_trsm(Prec::F64, false, false, false, sc.up(t1), nb, maxn, s);
+        launch_copy(Prec::F64, Prec::F64, true, sc.up(tr), nb, maxn, maxn, s);
+        launch_trsm(Prec::F64, false, false, false, sc.up(t2), nb, maxn, s);
+        G = G2;
+      }
+      // far-field block row Gram K(cand, samples) K(cand, samples)^T
+      std::vector<int> cand_all, samp_all;
+      std::vector<size_t> co(nb + 1, 0), sof(nb + 1, 0);
+      for (int g = 0; g < nb; ++g) {
+        const BoxRef& b = ht.ref[g];
+        const Problem& pb = h.probs[b.prob];
+        far_samples(pb.t, b.level, b.local, h.opt.far_s0, h.opt.far_smin, samp);
+        for (int64_t q : samp) samp_all.push_back((int)(pb.off + q));
+        sof[g + 1] = samp_all.size();
+        cand_all.insert(cand_all.end(), ht.cand[g].begin(), ht.cand[g].end());
+        co[g + 1] = cand_all.size();
+      }
+      int* dc = sc.up(cand_all);
+      int* ds = sc.up(samp_all);
+      std::vector<KgramTask> kt;
+      for (int g = 0; g < nb; ++g) {
+        int m = (int)(sof[g + 1] - sof[g]);
+        if (m == 0) continue;
+        kt.push_back(KgramTask{dc + co[g], ds + sof[g], G + off[g], n[g], m, n[g], 1});
+      }
+      launch_kgram(W, sc.up(kt), (int)kt.size(), maxn, pts, h.kp, s);
+    }
+    double* R = (double*)sc.alloc(NN * 8);
+    int* piv = (int*)sc.alloc((size_t)nb * 256 * 4);
+    int* rank = (int*)sc.alloc((size_t)nb * 4);
+    {
+      std::vector<CholTask> ct;
+      for (int g = 0; g < nb; ++g)
+        ct.push_back(CholTask{G + off[g], n[g], n[g], piv + (size_t)g * 256, R + off[g], rank + g, h.opt.tol,
+                              h.opt.max_rank});
+      launch_pchol(sc.up(ct), nb, s);
+    }
+    std::vector<int> hr(nb), hpiv((size_t)nb * 256);
+    H2_CUDA(cudaMemcpyAsync(hr.data(), rank, nb * 4, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaMemcpyAsync(hpiv.data(), piv, hpiv.size() * 4, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    ht.r.resize(nb);
+    ht.sk.resize(nb);
+    std::vector<int> keep_all(nb, 0);
+    for (int g = 0; g < nb; ++g) {
+      if (hr[g] == 0) {   // empty block row: nothing is redundant
+        keep_all[g] = 1;
+        hr[g] = n[g];
+        for (int q = 0; q < n[g]; ++q) hpiv[(size_t)g * 256 + q] = q;
+      }
+      ht.r[g] = hr[g];
+      ht.sk[g].resize(hr[g]);
+      for (int q = 0; q < hr[g]; ++q) ht.sk[g][q] = ht.cand[g][hpiv[(size_t)g * 256 + q]];
+    }
+    if (std::count(keep_all.begin(), keep_all.end(), 1))
+      H2_CUDA(cudaMemcpyAsync(piv, hpiv.data(), hpiv.size() * 4, cudaMemcpyHostToDevice, s));
+    std::vector<int>& r = ht.r;
+    std::vector<int> m(nb);
+    for (int g = 0; g < nb; ++g) m[g] = n[g] - r[g];
+    // interpolation matrix P (n x r, FP64): T = R11^-1 R12
+    double* P = (double*)sc.alloc(NN * 8, true);
+    {
+      std::vector<TrsmTask> tt;
+      std::vector<InterpTask> it;
+      std::vector<CopyTask> eye;
+      int maxrhs = 0;
+      for (int g = 0; g < nb; ++g) {
+        if (keep_all[g]) continue;
+        if (r[g] < n[g]) {
+          tt.push_back(TrsmTask{R + off[g], R + off[g] + (size_t)r[g] * n[g], r[g], n[g] - r[g], n[g], n[g], nullptr});
+          maxrhs = std::max(maxrhs, n[g] - r[g]);
+        }
+        it.push_back(InterpTask{piv + (size_t)g * 256, R + off[g] + (size_t)r[g] * n[g], P + off[g], n[g], r[g], n[g]});
+      }
+      launch_trsm(Prec::F64, false, false, false, sc.up(tt), (int)tt.size(), maxrhs, s);
+      launch_interp(Prec::F64, sc.up(it), (int)it.size(), s);
+      for (int g = 0; g < nb; ++g)
+        if (keep_all[g]) launch_fill_eye(Prec::F64, P + off[g], n[g], n[g], s);
+    }
+    // basis matrix in level coordinates: M = T P (n x r)
+    double* Mm = P;
+    if (H > 0) {
+      Mm = (double*)sc.alloc(NN * 8);
+      GemmBatch gb;
+      for (int g = 0; g < nb; ++g)
+        gb.add1(Mm + off[g], n[g], n[g], r[g], Tcur->as<double>() + t_off[g], n[g], P + off[g], n[g], n[g]);
+      gb.run(Prec::F64, false, false, sc);
+    }
+    // orthogonalise: Q = [U^R U^S], W (r x r)
+    ht.q_off = off;
+    ht.Q = std::make_shared<DBuf>(NN * 8);
+    ht.w_off.assign(nb + 1, 0);
+    for (int g = 0; g < nb; ++g) ht.w_off[g + 1] = ht.w_off[g] + (size_t)r[g] * r[g];
+    ht.W = std::make_shared<DBuf>(std::max<size_t>(1, ht.w_off[nb]) * 8);
+    {
+      double* V = (double*)sc.alloc(NN * 8);
+      std::vector<HqrTask> qt;
+      for (int g = 0; g < nb; ++g)
+        qt.push_back(HqrTask{Mm + off[g], V + off[g], ht.Q->as<double>() + off[g], ht.W->as<double>() + ht.w_off[g], n[g], r[g]});
+      launch_hqr(Prec::F64, sc.up(qt), nb, s);
+    }
+    const void* Qw = ht.Q->p;
+    const void* Ww = ht.W->p;
+    if (W == Prec::F32) {
+      ht.Qw = std::make_shared<DBuf>(NN * 4);
+      auto Wf = std::make_shared<DBuf>(std::max<size_t>(1, ht.w_off[nb]) * 4);
+      std::vector<CopyTask> ct, cw;
+      for (int g = 0; g < nb; ++g) {
+        ct.push_back(CopyTask{ht.Q->as<double>() + off[g], ht.Qw->as<float>() + off[g], n[g], n[g], n[g], n[g]});
+        cw.push_back(CopyTask{ht.W->as<double>() + ht.w_off[g], Wf->as<float>() + ht.w_off[g], r[g], r[g], r[g], r[g]});
+      }
+      launch_copy(Prec::F64, Prec::F32, false, sc.up(ct), nb, maxn, maxn, s);
+      launch_copy(Prec::F64, Prec::F32, false, sc.up(cw), nb, 256, 256, s);
+      sc.bufs.push_back(Wf);
+      Qw = ht.Qw->p;
+      Ww = Wf->p;
+    }
+    auto Qp = [&](int g) -> const char* { return (const char*)Qw + off[g] * ws; };
+    auto USp = [&](int g) -> const char* { return (const char*)Qw + (off[g] + (size_t)m[g] * n[g]) * ws; };
+    auto Wp = [&](int g) -> const char* { return (const char*)Ww + ht.w_off[g] * ws; };
+    // ---------------- parent-level storage (merge target) ---------------
+    Height* up = (H + 1 < h.Hmax) ? &h.hs[H + 1] : nullptr;
+    std::vector<std::vector<PairRef>> Anext;
+    DBufP Anext_buf;
+    if (up) {
+      up->n.assign(up->nb, 0);
+      up->cand.assign(up->nb, {});
+      for (int g = 0; g < nb; ++g) {
+        int pg = ht.parent[g];
+        if (pg < 0) continue;
+        up->n[pg] += r[g];
+        up->cand[pg].insert(up->cand[pg].end(), ht.sk[g].begin(), ht.sk[g].end());
+      }
+      size_t tot = 0;
+      std::vector<std::vector<size_t>> po(up->nb);
+      for (int pg = 0; pg < up->nb; ++pg)
+        for (int qg : up->near[pg]) {
+          po[pg].push_back(tot);
+          tot += (size_t)up->n[pg] * up->n[qg];
+        }
+      Anext_buf = std::make_shared<DBuf>(std::max<size_t>(1, tot) * ws);
+      Anext.assign(up->nb, {});
+      for (int pg = 0; pg < up->nb; ++pg)
+        for (size_t q = 0; q < up->near[pg].size(); ++q)
+          Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[pg][q] * ws, up->n[pg]});
+    }
+    // root setup for problems whose top ULV height is H
+    for (size_t p = 0; p < h.probs.size(); ++p) {
+      Problem& pb = h.probs[p];
+      if (pb.H != H + 1) continue;
+      std::vector<int> sizes(pb.t.boxes[pb.t.ltop].size(), 0);
+      for (int g = 0; g < nb; ++g)
+        if (ht.ref[g].prob == (int)p) sizes[ht.root_slot[g]] += r[g];
+      setup_root(pb, sizes);
+    }
+    // destination of the S^SS block of child pair (g, j): the parent block
+    // (or root matrix) at the children's quadrant
+    auto dest = [&](int g, int j, int& ld) -> char* {
+      int pg = ht.parent[g];
+      int rowoff = (ht.ref[g].local % 2) ? r[g - 1] : 0;
+      int coloff = (ht.ref[j].local % 2) ? r[j - 1] : 0;
+      if (pg >= 0) {
+        int pj = ht.parent[j];
+        const auto& nl = up->near[pg];
+        int q = (int)(std::find(nl.begin(), nl.end(), pj) - nl.begin());
+        ld = Anext[pg][q].ld;
+        return (char*)Anext[pg][q].ptr + ((size_t)rowoff + (size_t)coloff * ld) * ws;
+      }
+      Root& rt = h.probs[ht.ref[g].prob].root;
+      ld = rt.n;
+      size_t ro = (size_t)rt.off[ht.root_slot[g]] + rowoff;
+      size_t co = (size_t)rt.off[ht.root_slot[j]] + coloff;
+      return (char*)rt.A->p + (ro + co * rt.n) * ws;
+    };
+    // ---------------- 3. projection (eq. rs, eq. ss) -------------------
+    void* Sw = sc.alloc(NN * ws);
+    {
+      GemmBatch g1, g2;
+      for (int g = 0; g < nb; ++g) {
+        int dq = diag_q(g);
+        g1.add1((char*)Tmp + so[g] * ws, n[g], n[g], n[g], Ablk[g][dq].ptr, Ablk[g][dq].ld, Qp(g), n[g], n[g]);
+        g2.add1((char*)Sw + off[g] * ws, n[g], n[g], n[g], Qp(g), n[g], (char*)Tmp + so[g] * ws, n[g], n[g]);
+      }
+      g1.run(W, false, false, sc);
+      g2.run(W, true, false, sc);
+    }
+    {
+      size_t maxdeg = 0;
+      for (int g = 0; g < nb; ++g) maxdeg = std::max(maxdeg, ht.near[g].size());
+      for (size_t k = 0; k < maxdeg; ++k) {
+        GemmBatch g1, g2;
+        for (int g = 0; g < nb; ++g) {
+          if (k >= ht.near[g].size()) continue;
+          int j = ht.near[g][k];
+          if (j == g) continue;
+          char* V = (char*)Tmp + so[g] * ws;   // n_g x r_j
+          g1.add1(V, n[g], n[g], r[j], Ablk[g][k].ptr, Ablk[g][k].ld, USp(j), n[j], n[j]);
+          int ld;
+          char* D = dest(g, j, ld);
+          g2.add1(D, ld, r[g], r[j], USp(g), n[g], V, n[g], n[g]);
+        }
+        g1.run(W, false, false, sc);
+        g2.run(W, true, false, sc);
+      }
+      // far pairs at this level: W_I K(sk_I, sk_J) W_J^T
+      size_t maxfar = 0;
+      for (int g = 0; g < nb; ++g) maxfar = std::max(maxfar, ht.far[g].size());
+      std::vector<int> sk_all;
+      std::vector<size_t> sko(nb + 1, 0);
+      for (int g = 0; g < nb; ++g) {
+        sk_all.insert(sk_all.end(), ht.sk[g].begin(), ht.sk[g].end());
+        sko[g + 1] = sk_all.size();
+      }
+      int* dsk = sc.up(sk_all);
+      for (size_t k = 0; k < maxfar; ++k) {
+        std::vector<AsmTask> at;
+        GemmBatch g1, g2;
+        int maxc = 0;
+        for (int g = 0; g < nb; ++g) {
+          if (k >= ht.far[g].size()) continue;
+          int j = ht.far[g][k];
+          char* Kb = (char*)Tmp + so[g] * ws;           // r_g x r_j
+          char* V = (char*)Mk + so[g] * ws;             // r_g x r_j
+          at.push_back(AsmTask{Kb, dsk + sko[g], dsk + sko[j], 0, 0, r[g], r[j], r[g]});
+          maxc = std::max(maxc, r[j]);
+          g1.add1(V, r[g], r[g], r[j], Wp(g), r[g], Kb, r[g], r[g]);
+          int ld;
+          char* D = dest(g, j, ld);
+          g2.add1(D, ld, r[g], r[j], V, r[g], Wp(j), r[j], r[j]);
+        }
+        launch_assemble(W, sc.up(at), (int)at.size(), 256, maxc, pts, h.kp, s);
+        g1.run(W, false, false, sc);
+        g2.run(W, false, true, sc);
+      }
+    }
+    // ---------------- 4. partial LU of S^RR (eq. lu) -------------------
+    ht.S = std::make_shared<DBuf>(NN * 8);
+    {
+      std::vector<CopyTask> ct;
+      for (int g = 0; g < nb; ++g)
+        ct.push_back(CopyTask{(char*)Sw + off[g] * ws, ht.S->as<double>() + off[g], n[g], n[g], n[g], n[g]});
+      launch_copy(W, Prec::F64, false, sc.up(ct), nb, maxn, maxn, s);
+    }
+    ht.pv_off.assign(nb + 1, 0);
+    ht.lt_off.assign(nb + 1, 0);
+    for (int g = 0; g < nb; ++g) {
+      ht.pv_off[g + 1] = ht.pv_off[g] + m[g];
+      ht.lt_off[g + 1] = ht.lt_off[g] + (size_t)m[g] * r[g];
+    }
+    ht.pivRR = std::make_shared<DBuf>(std::max<size_t>(1, ht.pv_off[nb]) * 4);
+    ht.Lt = std::make_shared<DBuf>(std::max<size_t>(1, ht.lt_off[nb]) * 8);
+    int* info = (int*)sc.alloc(4, true);
+    {
+      double* S = ht.S->as<double>();
+      std::vector<LuTask> lu;
+      std::vector<TrsmTask> trs, tsr;
+      std::vector<CopyTask> tr;
+      int maxr = 0, maxm = 0;
+      for (int g = 0; g < nb; ++g) {
+        if (m[g] == 0) continue;
+        double* Sg = S + off[g];
+        lu.push_back(LuTask{Sg, m[g], m[g], n[g], ht.pivRR->as<int>() + ht.pv_off[g], info});
+        trs.push_back(TrsmTask{Sg, Sg + (size_t)m[g] * n[g], m[g], r[g], n[g], n[g], ht.pivRR->as<int>() + ht.pv_off[g]});
+        // (L^SR)^T = U^-T (S^SR)^T: transpose S^SR (r x m) into Lt (m x r)
+        tr.push_back(CopyTask{Sg + m[g], ht.Lt->as<double>() + ht.lt_off[g], m[g], r[g], n[g], m[g]});
+        tsr.push_back(TrsmTask{Sg, ht.Lt->as<double>() + ht.lt_off[g], m[g], r[g], n[g], m[g], nullptr});
+        maxr = std::max(maxr, r[g]);
+        maxm = std::max(maxm, m[g]);
+      }
+      if (!lu.empty()) {
+        launch_getrf(Prec::F64, sc.up(lu), (int)lu.size(), s);
+        launch_trsm(Prec::F64, true, true, false, sc.up(trs), (int)trs.size(), maxr, s);
+        launch_copy(Prec::F64, Prec::F64, true, sc.up(tr), (int)tr.size(), maxm, maxr, s);
+        launch_trsm(Prec::F64, true, false, true, sc.up(tsr), (int)tsr.size(), maxr, s);
+        // Schur: S^SS -= (L^SR) U^RS = Lt^T U^RS
+        GemmBatch gb;
+        for (int g = 0; g < nb; ++g) {
+          if (m[g] == 0) continue;
+          double* Sg = S + off[g];
+          double* SS = Sg + m[g] + (size_t)m[g] * n[g];
+          gb.add1(SS, n[g], r[g], r[g], ht.Lt->as<double>() + ht.lt_off[g], m[g], Sg + (size_t)m[g] * n[g], n[g], m[g],
+                  -1.0, 1.0);
+        }
+        gb.run(Prec::F64, true, false, sc);
+      }
+      // S^SS_II -> parent quadrant
+      std::vector<CopyTask> cs;
+      for (int g = 0; g < nb; ++g) {
+        int ld;
+        char* D = dest(g, g, ld);
+        cs.push_back(CopyTask{S + off[g] + m[g] + (size_t)m[g] * n[g], D, r[g], r[g], n[g], ld});
+      }
+      launch_copy(Prec::F64, W, false, sc.up(cs), nb, 256, 256, s);
+    }
+    int hinfo = 0;
+    H2_CUDA(cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    if (hinfo != 0) throw StatusError(H2_ERR_SINGULAR, "zero pivot in a redundant-block LU");
+    // ---------------- 5. next height: T = blockdiag(W_a, W_b) ---------
+    if (up) {
+      std::vector<size_t> to(up->nb + 1, 0);
+      for (int pg = 0; pg < up->nb; ++pg) to[pg + 1] = to[pg] + (size_t)up->n[pg] * up->n[pg];
+      auto Tn = std::make_shared<DBuf>(std::max<size_t>(1, to[up->nb]) * 8);
+      H2_CUDA(cudaMemsetAsync(Tn->p, 0, Tn->bytes, s));
+      std::vector<CopyTask> ct;
+      for (int g = 0; g < nb; ++g) {
+        int pg = ht.parent[g];
+        if (pg < 0) continue;
+        int o = (ht.ref[g].local % 2) ? r[g - 1] : 0;
+        ct.push_back(CopyTask{ht.W->as<double>() + ht.w_off[g], Tn->as<double>() + to[pg] + o + (size_t)o * up->n[pg],
+                              r[g], r[g], r[g], up->n[pg]});
+      }
+      launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 256, 256, s);
+      H2_CUDA(cudaStreamSynchronize(s));
+      Tcur = Tn;
+      t_off = to;
+      Ablk = std::move(Anext);
+      Aown.clear();
+      Aown.push_back(Anext_buf);
+    }
+    // level-vector offsets (solve)
+    ht.v_off.assign(nb + 1, 0);
+    for (int g = 0; g < nb; ++g) ht.v_off[g + 1] = ht.v_off[g] + n[g];
+    ht.v_len = ht.v_off[nb];
+    H2_CUDA(cudaStreamSynchronize(s));
+    h.level_ms.push_back(now_ms() - t0);
+  }
+  // roots
+  for (auto& pb : h.probs) {
+    Root& rt = pb.root;
+    if (rt.n == 0) continue;
+    Scratch sc(s);
+    std::vector<CopyTask> ct{CopyTask{rt.A->p, rt.LU->p, rt.n, rt.n, rt.n, rt.n}};
+    launch_copy(W, Prec::F64, false, sc.up(ct), 1, rt.n, rt.n, s);
+    root_factor(h, rt, spd);
+    rt.A.reset();
+  }
+  H2_CUDA(cudaStreamSynchronize(s));
+}
+
+// -------------------------------------------------------------- solve ----
+// x = ULV^-1 b in tree order (N x nrhs, ld = Ntot), FP64 sweeps.
+static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
+  cudaStream_t s = h.s;
+  Scratch sc(s);
+  const int64_t ld = h.Ntot;
+  std::vector<double*> c(h.Hmax), xo(h.Hmax);
+  for (int H = 0; H < h.Hmax; ++H) {
+    c[H] = (double*)sc.alloc((size_t)h.hs[H].v_len * nrhs * 8);
+    xo[H] = (double*)sc.alloc((size_t)h.hs[H].v_len * nrhs * 8);
+  }
+  std::vector<double*> rootb(h.probs.size(), nullptr), rootx(h.probs.size(), nullptr);
+  for (size_t p = 0; p < h.probs.size(); ++p)
+    if (h.probs[p].root.n) {
+      rootb[p] = (double*)sc.alloc((size_t)h.probs[p].root.n * nrhs * 8);
+      rootx[p] = (double*)sc.alloc((size_t)h.probs[p].root.n * nrhs * 8);
+    }
+  // problems without ULV heights: root rhs = the whole problem
+  {
+    std::vector<CopyTask> ct;
+    for (size_t p = 0; p < h.probs.size(); ++p)
+      if (h.probs[p].H == 0)
+        ct.push_back(CopyTask{b + h.probs[p].off, rootb[p], h.probs[p].root.n, nrhs, (int)ld, h.probs[p].root.n});
+    launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 8192, nrhs, s);
+  }
+  // forward sweep
+  for (int H = 0; H < h.Hmax; ++H) {
+    Height& ht = h.hs[H];
+    const int nb = ht.nb;
+    const int64_t lv = ht.v_len;
+    GemmBatch g1;
+    for (int g = 0; g < nb; ++g) {
+      const double* src;
+      int64_t lds;
+      if (H == 0) {
+        const BoxRef& bb = ht.ref[g];
+        const Problem& pb = h.probs[bb.prob];
+        src = b + pb.off + pb.t.boxes[bb.level][bb.local].s;
+        lds = ld;
+      } else {
+        src = xo[H - 1] + ht.v_off[g];   // gathered into xo[H-1] below, by parent offsets
+        lds = ht.v_len;
+      }
+      g1.add1(c[H] + ht.v_off[g], (int)lv, ht.n[g], nrhs, ht.Q->as<double>() + ht.q_off[g], ht.n[g], src, (int)lds,
+              ht.n[g]);
+    }
+    g1.run(Prec::F64, true, false, sc);
+    std::vector<TrsmTask> tl;
+    GemmBatch g2;
+    for (int g = 0; g < nb; ++g) {
+      int m = ht.n[g] - ht.r[g];
+      if (m == 0) continue;
+      double* Sg = ht.S->as<double>() + ht.q_off[g];
+      tl.push_back(TrsmTask{Sg, c[H] + ht.v_off[g], m, nrhs, ht.n[g], (int)lv, ht.pivRR->as<int>() + ht.pv_off[g]});
+      g2.add1(c[H] + ht.v_off[g] + m, (int)lv, ht.r[g], nrhs, ht.Lt->as<double>() + ht.lt_off[g], m,
+              c[H] + ht.v_off[g], (int)lv, m, -1.0, 1.0);
+    }
+    launch_trsm(Prec::F64, true, true, false, sc.up(tl), (int)tl.size(), nrhs, s);
+    g2.run(Prec::F64, true, false, sc);
+    // gather skeleton parts into the next height's input (stored in xo[H])
+    std::vector<CopyTask> ct;
+    for (int g = 0; g < nb; ++g) {
+      int m = ht.n[g] - ht.r[g];
+      int o = (ht.ref[g].local % 2) ? ht.r[g - 1] : 0;
+      if (ht.parent[g] >= 0) {
+        const Height& up = h.hs[H + 1];
+        ct.push_back(CopyTask{c[H] + ht.v_off[g] + m, xo[H] + up.v_off[ht.parent[g]] + o, ht.r[g], nrhs, (int)lv,
+                              (int)up.v_len});
+      } else {
+        Root& rt = h.probs[ht.ref[g].prob].root;
+        ct.push_back(CopyTask{c[H] + ht.v_off[g] + m, rootb[ht.ref[g].prob] + rt.off[ht.root_slot[g]] + o, ht.r[g],
+                              nrhs, (int)lv, rt.n});
+      }
+    }
+    if (H + 1 < h.Hmax) {
+      // xo[H] is sized by height H; the parent vector is shorter, fits
+    }
+    launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 256, nrhs, s);
+  }
+  // root solves
+  {
+    GemmBatch gb;
+    for (size_t p = 0; p < h.probs.size(); ++p) {
+      Root& rt = h.probs[p].root;
+      if (!rt.n) continue;
+      gb.add1(rootx[p], rt.n, rt.n, nrhs, rt.inv->p, rt.n, rootb[p], rt.n, rt.n);
+    }
+    gb.run(Prec::F64, false, false, sc);
+  }
+  {
+    std::vector<CopyTask> ct;
+    for (size_t p = 0; p < h.probs.size(); ++p)
+      if (h.probs[p].H == 0)
+        ct.push_back(CopyTask{rootx[p], x + h.probs[p].off, h.probs[p].root.n, nrhs, h.probs[p].root.n, (int)ld});
+    launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 8192, nrhs, s);
+  }
+  // backward sweep
+  for (int H = h.Hmax - 1; H >= 0; --H) {
+    Height& ht = h.hs[H];
+    const int nb = ht.nb;
+    const int64_t lv = ht.v_len;
+    std::vector<CopyTask> ct;
+    for (int g = 0; g < nb; ++g) {
+      int m = ht.n[g] - ht.r[g];
+      int o = (ht.ref[g].local % 2) ? ht.r[g - 1] : 0;
+      const double* src;
+      int lds;
+      if (ht.parent[g] >= 0) {
+        const Height& up = h.hs[H + 1];
+        src = xo[H + 1] + up.v_off[ht.parent[g]] + o;
+        lds = (int)up.v_len;
+      } else {
+        Root& rt = h.probs[ht.ref[g].prob].root;
+        src = rootx[ht.ref[g].prob] + rt.off[ht.root_slot[g]] + o;
+        lds = rt.n;
+      }
+      ct.push_back(CopyTask{src, c[H] + ht.v_off[g] + m, ht.r[g], nrhs, lds, (int)lv});
+    }
+    launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 256, nrhs, s);
+    GemmBatch g1;
+    std::vector<TrsmTask> tu;
+    for (int g = 0; g < nb; ++g) {
+      int m = ht.n[g] - ht.r[g];
+      if (m == 0) continue;
+      double* Sg = ht.S->as<double>() + ht.q_off[g];
+      g1.add1(c[H] + ht.v_off[g], (int)lv, m, nrhs, Sg + (size_t)m * ht.n[g], ht.n[g], c[H] + ht.v_off[g] + m, (int)lv,
+              ht.r[g], -1.0, 1.0);
+      tu.push_back(TrsmTask{Sg, c[H] + ht.v_off[g], m, nrhs, ht.n[g], (int)lv, nullptr});
+    }
+    g1.run(Prec::F64, false, false, sc);
+    launch_trsm(Prec::F64, false, false, false, sc.up(tu), (int)tu.size(), nrhs, s);
+    GemmBatch g2;
+    for (int g = 0; g < nb; ++g) {
+      double* dst;
+      int ldd;
+      if (H == 0) {
+        const BoxRef& bb = ht.ref[g];
+        const Problem& pb = h.probs[bb.prob];
+        dst = x + pb.off + pb.t.boxes[bb.level][bb.local].s;
+        ldd = (int)ld;
+      } else {
+        dst = xo[H] + ht.v_off[g];
+        ldd = (int)lv;
+      }
+      g2.add1(dst, ldd, ht.n[g], nrhs, ht.Q->as<double>() + ht.q_off[g], ht.n[g], c[H] + ht.v_off[g], (int)lv, ht.n[g]);
+    }
+    g2.run(Prec::F64, false, false, sc);
+  }
+  H2_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace h2
+
+// ================================================================= C ABI ==
+using namespace h2;
+
+static thread_local std::string g_err;
+
+struct h2_handle_ {
+  Handle h;
+};
+
+template <class F> static h2_status guard(F&& f) {
+  try {
+    f();
+    return H2_OK;
+  } catch (const StatusError& e) {
+    g_err = e.what();
+    return (h2_status)e.status;
+  } catch (const CudaError& e) {
+    g_err = e.what();
+    return H2_ERR_DEVICE;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return H2_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return H2_ERR_DEVICE;
+  }
+}
+
+static void check_opts(const h2_kernel* k, const h2_options* o) {
+  if (!k || !o) throw StatusError(H2_ERR_ARG, "null kernel or options");
+  if (k->kind < 0 || k->kind > 2) throw StatusError(H2_ERR_ARG, "unknown kernel kind");
+  if (!(o->eta > 0)) throw StatusError(H2_ERR_ARG, "eta must be > 0");
+  if (o->leaf < 1 || o->leaf > 256) throw StatusError(H2_ERR_ARG, "leaf must be in [1, 256]");
+  if (o->max_rank < 1 || o->max_rank > 128) throw StatusError(H2_ERR_ARG, "max_rank must be in [1, 128]");
+  if (!(o->tol >= 0) || !std::isfinite(o->tol)) throw StatusError(H2_ERR_ARG, "tol must be finite and >= 0");
+  if (o->far_s0 < 0 || o->far_smin < 0) throw StatusError(H2_ERR_ARG, "far sample sizes must be >= 0");
+}
+
+static void construct_impl(h2_handle_* H, int P, const double* const* points, const int64_t* N,
+                           const h2_kernel* kern, const h2_options* opt, void* stream) {
+  check_opts(kern, opt);
+  Handle& h = H->h;
+  h.s = (cudaStream_t)stream;
+  h.kp = KParams{kern->kind, kern->delta, kern->kappa, kern->ell, kern->nugget};
+  h.opt = *opt;
+  double t0 = now_ms();
+  h.probs.resize(P);
+  int64_t off = 0;
+  std::vector<double> host;
+  for (int p = 0; p < P; ++p) {
+    if (N[p] < 1) throw StatusError(H2_ERR_ARG, "N must be >= 1");
+    if (N[p] > (int64_t)1 << 30) throw StatusError(H2_ERR_ARG, "N too large");
+    if (!points[p]) throw StatusError(H2_ERR_ARG, "null points");
+    host.resize((size_t)N[p] * 3);
+    if (is_device_ptr(points[p])) {
+      H2_CUDA(cudaMemcpy(host.data(), points[p], host.size() * 8, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(host.data(), points[p], host.size() * 8);
+    }
+    for (double v : host)
+      if (!std::isfinite(v)) throw StatusError(H2_ERR_NONFINITE, "non-finite coordinate");
+    Problem& pb = h.probs[p];
+    pb.t = build_tree(host.data(), N[p], opt->leaf, opt->eta);
+    pb.off = off;
+    pb.H = pb.t.L - pb.t.ltop;
+    off += N[p];
+  }
+  h.Ntot = off;
+  if (h.Ntot > ((int64_t)1 << 31) - 1) throw StatusError(H2_ERR_ARG, "total N too large");
+  // tree-order points and the permutation
+  std::vector<double> xs(h.Ntot), ys(h.Ntot), zs(h.Ntot);
+  std::vector<int64_t> perm(h.Ntot);
+  for (auto& pb : h.probs) {
+    for (int64_t q = 0; q < pb.t.N; ++q) {
+      xs[pb.off + q] = pb.t.xt[q];
+      ys[pb.off + q] = pb.t.yt[q];
+      zs[pb.off + q] = pb.t.zt[q];
+      perm[pb.off + q] = pb.off + pb.t.perm[q];
+    }
+  }
+  h.px.alloc(h.Ntot * 8);
+  h.py.alloc(h.Ntot * 8);
+  h.pz.alloc(h.Ntot * 8);
+  h.perm.alloc(h.Ntot * 8);
+  H2_CUDA(cudaMemcpy(h.px.p, xs.data(), h.Ntot * 8, cudaMemcpyHostToDevice));
+  H2_CUDA(cudaMemcpy(h.py.p, ys.data(), h.Ntot * 8, cudaMemcpyHostToDevice));
+  H2_CUDA(cudaMemcpy(h.pz.p, zs.data(), h.Ntot * 8, cudaMemcpyHostToDevice));
+  H2_CUDA(cudaMemcpy(h.perm.p, perm.data(), h.Ntot * 8, cudaMemcpyHostToDevice));
+  build_heights(h);
+  build_operator(h);
+  h.t_construct_ms = now_ms() - t0;
+}
+
+extern "C" {
+
+h2_status h2_construct(const double* points, int64_t N, const h2_kernel* kern, const h2_options* opt,
+                       void* stream, h2_handle* out) {
+  if (!out) {
+    g_err = "null output handle";
+    return H2_ERR_ARG;
+  }
+  *out = nullptr;
+  auto* H = new h2_handle_();
+  h2_status st = guard([&] { construct_impl(H, 1, &points, &N, kern, opt, stream); });
+  if (st != H2_OK) {
+    delete H;
+    return st;
+  }
+  *out = H;
+  return H2_OK;
+}
+
+h2_status h2_construct_batched(int32_t P, const double* const* points, const int64_t* N, const h2_kernel* kern,
+                               const h2_options* opt, void* stream, h2_handle* out) {
+  if (!out || P < 1 || !points || !N) {
+    g_err = "invalid batched arguments";
+    return H2_ERR_ARG;
+  }
+  *out = nullptr;
+  auto* H = new h2_handle_();
+  h2_status st = guard([&] { construct_impl(H, P, points, N, kern, opt, stream); });
+  if (st != H2_OK) {
+    delete H;
+    return st;
+  }
+  *out = H;
+  return H2_OK;
+}
+
+h2_status h2_factor(h2_handle H, int32_t precision, int32_t spd) {
+  if (!H) {
+    g_err = "null handle";
+    return H2_ERR_ARG;
+  }
+  if (precision != H2_FP64 && precision != H2_MIXED) {
+    g_err = "unknown precision";
+    return H2_ERR_ARG;
+  }
+  return guard([&] {
+    Handle& h = H->h;
+    h.factored = false;
+    double t0 = now_ms();
+    factor(h, precision, spd);
+    h.t_factor_ms = now_ms() - t0;
+    h.precision = precision;
+    h.spd = spd;
+    h.factored = true;
+  });
+}
+
+// Copy a caller vector block (host or device, user order) into tree order.
+static void to_tree(Handle& h, const double* src, int64_t ld, int nrhs, double* dst_tree, Scratch& sc) {
+  const double* d = src;
+  if (!is_device_ptr(src)) {
+    double* tmp = (double*)sc.alloc((size_t)ld * nrhs * 8);
+    H2_CUDA(cudaMemcpyAsync(tmp, src, (size_t)ld * nrhs * 8, cudaMemcpyHostToDevice, h.s));
+    d = tmp;
+  }
+  launch_permute_rows(d, ld, dst_tree, h.Ntot, h.perm.as<int64_t>(), h.Ntot, nrhs, false, h.s);
+}
+
+static void from_tree(Handle& h, const double* src_tree, double* dst, int64_t ld, int nrhs, Scratch& sc) {
+  if (is_device_ptr(dst)) {
+    launch_permute_rows(src_tree, h.Ntot, dst, ld, h.perm.as<int64_t>(), h.Ntot, nrhs, true, h.s);
+  } else {
+    double* tmp = (double*)sc.alloc((size_t)ld * nrhs * 8);
+    launch_permute_rows(src_tree, h.Ntot, tmp, ld, h.perm.as<int64_t>(), h.Ntot, nrhs, true, h.s);
+    H2_CUDA(cudaMemcpyAsync(dst, tmp, (size_t)ld * nrhs * 8, cudaMemcpyDeviceToHost, h.s));
+  }
+  H2_CUDA(cudaStreamSynchronize(h.s));
+}
+
+h2_status h2_matvec(h2_handle H, const double* x, double* y, int32_t nrhs, int64_t ld) {
+  if (!H || !x || !y || nrhs < 1 || ld < H->h.Ntot) {
+    g_err = "invalid matvec arguments";
+    return H2_ERR_ARG;
+  }
+  return guard([&] {
+    Handle& h = H->h;
+    Scratch sc(h.s);
+    double* xt = (double*)sc.alloc((size_t)h.Ntot * nrhs * 8);
+    double* yt = (double*)sc.alloc((size_t)h.Ntot * nrhs * 8);
+    to_tree(h, x, ld, nrhs, xt, sc);
+    matvec_tree(h, xt, yt, nrhs);
+    from_tree(h, yt, y, ld, nrhs, sc);
+  });
+}
+
+h2_status h2_solve(h2_handle H, const double* b, double* x, int32_t nrhs, int64_t ld, double target,
+                   int32_t max_iter, double* achieved, int32_t* iters) {
+  if (!H || !b || !x || nrhs < 1 || ld < H->h.Ntot || max_iter < 0) {
+    g_err = "invalid solve arguments";
+    return H2_ERR_ARG;
+  }
+  if (!H->h.factored) {
+    g_err = "h2_solve before h2_factor";
+    return H2_ERR_STATE;
+  }
+  bool converged = true;
+  h2_status st = guard([&] {
+    Handle& h = H->h;
+    Scratch sc(h.s);
+    const int64_t N = h.Ntot;
+    double* bt = (double*)sc.alloc((size_t)N * nrhs * 8);
+    double* xt = (double*)sc.alloc((size_t)N * nrhs * 8);
+    double* rt = (double*)sc.alloc((size_t)N * nrhs * 8);
+    double* dt = (double*)sc.alloc((size_t)N * nrhs * 8);
+    double* nrm = (double*)sc.alloc((size_t)nrhs * 8 * 2);
+    to_tree(h, b, ld, nrhs, bt, sc);
+    launch_colnorm2(bt, (int)N, nrhs, N, nrm, h.s);
+    std::vector<double> bn(nrhs), rn(nrhs);
+    H2_CUDA(cudaMemcpyAsync(bn.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
+    H2_CUDA(cudaStreamSynchronize(h.s));
+    for (double v : bn)
+      if (!std::isfinite(v)) throw StatusError(H2_ERR_NONFINITE, "non-finite right-hand side");
+    ulv_solve_tree(h, bt, xt, nrhs);
+    int it = 0;
+    std::vector<double> rel(nrhs, 0.0);
+    while (true) {
+      matvec_tree(h, xt, rt, nrhs);
+      // r = b - A x
+      launch_axpy_cols(rt, bt, (int)N, nrhs, N, N, -1.0, h.s);   // rt = A x - b
+      launch_colnorm2(rt, (int)N, nrhs, N, nrm, h.s);
+      H2_CUDA(cudaMemcpyAsync(rn.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
+      H2_CUDA(cudaStreamSynchronize(h.s));
+      bool ok = true;
+      for (int c = 0; c < nrhs; ++c) {
+        double den = bn[c] > 0 ? std::sqrt(bn[c]) : 1.0;
+        rel[c] = std::sqrt(rn[c]) / den;
+        if (!(rel[c] <= target)) ok = false;
+      }
+      if (ok || it >= max_iter) {
+        converged = ok;
+        break;
+      }
+      // x <- x - ULV^-1 (A x - b)
+      ulv_solve_tree(h, rt, dt, nrhs);
+      launch_axpy_cols(xt, dt, (int)N, nrhs, N, N, -1.0, h.s);
+      ++it;
+    }
+    from_tree(h, xt, x, ld, nrhs, sc);
+    if (achieved)
+      for (int c = 0; c < nrhs; ++c) achieved[c] = rel[c];
+    if (iters) *iters = it;
+  });
+  if (st == H2_OK && !converged) {
+    g_err = "refinement did not reach the target residual";
+    return H2_ERR_NOT_CONVERGED;
+  }
+  return st;
+}
+
+h2_status h2_logdet(h2_handle H, double* log_abs_det, int32_t* sign) {
+  if (!H || !log_abs_det) {
+    g_err = "invalid logdet arguments";
+    return H2_ERR_ARG;
+  }
+  if (!H->h.factored) {
+    g_err = "h2_logdet before h2_factor";
+    return H2_ERR_STATE;
+  }
+  return guard([&] {
+    Handle& h = H->h;
+    Scratch sc(h.s);
+    std::vector<double> ld(h.probs.size(), 0.0), sg(h.probs.size(), 1.0);
+    for (int Hh = 0; Hh < h.Hmax; ++Hh) {
+      Height& ht = h.hs[Hh];
+      std::vector<LuTask> lt;
+      std::vector<int> who;
+      for (int g = 0; g < ht.nb; ++g) {
+        int m = ht.n[g] - ht.r[g];
+        if (m == 0) continue;
+        lt.push_back(LuTask{ht.S->as<double>() + ht.q_off[g], m, m, ht.n[g], ht.pivRR->as<int>() + ht.pv_off[g], nullptr});
+        who.push_back(ht.ref[g].prob);
+      }
+      if (lt.empty()) continue;
+      double* o = (double*)sc.alloc(lt.size() * 16);
+      launch_logdet_lu(sc.up(lt), (int)lt.size(), o, o + lt.size(), false, h.s);
+      std::vector<double> ho(lt.size() * 2);
+      H2_CUDA(cudaMemcpyAsync(ho.data(), o, ho.size() * 8, cudaMemcpyDeviceToHost, h.s));
+      H2_CUDA(cudaStreamSynchronize(h.s));
+      for (size_t i = 0; i < lt.size(); ++i) {
+        ld[who[i]] += ho[i];
+        sg[who[i]] *= ho[lt.size() + i];
+      }
+    }
+    for (size_t p = 0; p < h.probs.size(); ++p) {
+      ld[p] += h.probs[p].root.logdet;
+      sg[p] *= h.probs[p].root.sign;
+      log_abs_det[p] = ld[p];
+      if (sign) sign[p] = sg[p] < 0 ? -1 : 1;
+    }
+  });
+}
+
+h2_status h2_stats(h2_handle H, char* json, size_t cap) {
+  if (!H || !json || cap == 0) {
+    g_err = "invalid stats arguments";
+    return H2_ERR_ARG;
+  }
+  return guard([&] {
+    Handle& h = H->h;
+    std::ostringstream o;
+    o << "{\"N\":" << h.Ntot << ",\"problems\":" << h.probs.size() << ",\"heights\":" << h.Hmax
+      << ",\"construct_ms\":" << h.t_construct_ms << ",\"factor_ms\":" << h.t_factor_ms << ",\"levels\":[";
+    for (int H2i = 0; H2i < h.Hmax; ++H2i) {
+      const Height& ht = h.hs[H2i];
+      double rs = 0, rmax = 0, ro = 0, nearc = 0, farc = 0;
+      for (int g = 0; g < ht.nb; ++g) {
+        if (!ht.r.empty()) {
+          rs += ht.r[g];
+          rmax = std::max(rmax, (double)ht.r[g]);
+        }
+        if (!ht.r_op.empty()) ro += ht.r_op[g];
+        nearc += ht.near[g].size();
+        farc += ht.far[g].size();
+      }
+      if (H2i) o << ",";
+      o << "{\"height\":" << H2i << ",\"boxes\":" << ht.nb << ",\"rank_mean\":" << (ht.nb ? rs / ht.nb : 0)
+        << ",\"rank_max\":" << rmax << ",\"op_rank_mean\":" << (ht.nb ? ro / ht.nb : 0)
+        << ",\"near_mean\":" << (ht.nb ? nearc / ht.nb : 0) << ",\"far_mean\":" << (ht.nb ? farc / ht.nb : 0);
+      if ((size_t)H2i < h.level_ms.size()) o << ",\"factor_ms\":" << h.level_ms[H2i];
+      o << "}";
+    }
+    o << "],\"roots\":[";
+    for (size_t p = 0; p < h.probs.size(); ++p) o << (p ? "," : "") << h.probs[p].root.n;
+    o << "]}";
+    std::string sj = o.str();
+    size_t n = std::min(cap - 1, sj.size());
+    std::memcpy(json, sj.data(), n);
+    json[n] = 0;
+  });
+}
+
+const char* h2_last_error(void) { return g_err.c_str(); }
+
+void h2_destroy(h2_handle H) { delete H; }
+
+}  // extern "C"

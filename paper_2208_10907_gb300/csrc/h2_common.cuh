@@ -1,0 +1,209 @@
+// Shared device definitions of the H^2-ULV CUDA library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace h2 {
+
+// ---------------------------------------------------------------------------
+// Error handling: CUDA errors become C++ exceptions inside the library and a
+// status code at the C ABI.
+// ---------------------------------------------------------------------------
+struct CudaError : std::runtime_error {
+  explicit CudaError(const std::string& s) : std::runtime_error(s) {}
+};
+struct StatusError : std::runtime_error {
+  int status;
+  StatusError(int st, const std::string& s) : std::runtime_error(s), status(st) {}
+};
+
+#define H2_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      throw ::h2::CudaError(std::string(#call) + ": " + cudaGetErrorString(e_) +      \
+                            " at " + __FILE__ + ":" + std::to_string(__LINE__));       \
+  } while (0)
+
+#define H2_LAUNCH_CHECK() H2_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// Kernel functions (Sec. IV Laplace Green's function, Sec. V Yukawa), with
+// the point singularity regularised by delta; Matern-3/2 for covariances.
+// ---------------------------------------------------------------------------
+struct KParams {
+  int kind;  // 0 laplace, 1 yukawa, 2 matern32
+  double delta, kappa, ell, nugget;
+};
+
+__device__ __forceinline__ double kernel_eval(const KParams& kp, double dx, double dy, double dz) {
+  double r2 = dx * dx + dy * dy + dz * dz;
+  double r = sqrt(r2);
+  if (kp.kind == 0) return 1.0 / (r + kp.delta);
+  if (kp.kind == 1) return exp(-kp.kappa * r) / (r + kp.delta);
+  double s = 1.7320508075688772 * r / kp.ell;
+  double v = (1.0 + s) * exp(-s);
+  return r2 == 0.0 ? v + kp.nugget : v;
+}
+
+__device__ __forceinline__ float kernel_eval_f(const KParams& kp, double dx, double dy, double dz) {
+  // coordinate differences in FP64 (close points keep their relative
+  // accuracy), the rest in FP32
+  float r2 = (float)(dx * dx + dy * dy + dz * dz);
+  float r = sqrtf(r2);
+  if (kp.kind == 0) return 1.0f / (r + (float)kp.delta);
+  if (kp.kind == 1) return expf(-(float)kp.kappa * r) / (r + (float)kp.delta);
+  float s = 1.7320508f * r / (float)kp.ell;
+  float v = (1.0f + s) * expf(-s);
+  return r2 == 0.0f ? v + (float)kp.nugget : v;
+}
+
+template <typename T> struct KEval;
+template <> struct KEval<double> {
+  static __device__ __forceinline__ double eval(const KParams& kp, double dx, double dy, double dz) {
+    return kernel_eval(kp, dx, dy, dz);
+  }
+};
+template <> struct KEval<float> {
+  static __device__ __forceinline__ float eval(const KParams& kp, double dx, double dy, double dz) {
+    return kernel_eval_f(kp, dx, dy, dz);
+  }
+};
+
+// Tree-order points, structure of arrays.
+struct Points {
+  const double* x;
+  const double* y;
+  const double* z;
+};
+
+// ---------------------------------------------------------------------------
+// Task descriptors of the batched kernels.  Matrices are column-major.
+// ---------------------------------------------------------------------------
+struct GemmTerm {
+  const void* A;
+  const void* B;
+  int K, lda, ldb;
+};
+struct GemmTask {
+  void* C;            // output
+  const void* Cin;    // beta * Cin is added (may alias C); null = no beta term
+  int M, N, ldc, ldcin;
+  int t0, nt;         // terms [t0, t0+nt)
+  double alpha, beta;
+};
+
+struct LuTask {        // in-place LU with partial pivoting of an m x nc panel
+  void* A;
+  int m, nc, lda;
+  int* piv;            // nc pivots (0-based row index within the panel)
+  int* info;           // set to k+1 at the first zero pivot (if non-null)
+};
+
+struct TrsmTask {      // B <- op(A)^-1 B, A n x n triangular, B n x nrhs
+  const void* A;
+  void* B;
+  int n, nrhs, lda, ldb;
+  const int* piv;      // row interchanges applied to B first (getrs), or null
+};
+
+struct CholTask {      // pivoted Cholesky of an n x n Gram matrix (in place)
+  double* G;
+  int n, ldg;
+  int* piv;            // n
+  double* R;           // n x n, ld n: rows 0..rank-1 hold R
+  int* rank;
+  double tol;
+  int max_rank;
+};
+
+struct PqrTask {       // Householder QR with column pivoting of an m x n matrix
+  double* A;
+  int m, n, lda;
+  int* piv;
+  double* R;           // n x n, ld n
+  int* rank;
+  double tol;
+  int max_rank;
+};
+
+struct HqrTask {       // QR of M (n x r): Q = [U^R U^S] (n x n), W (r x r)
+  void* M;             // n x r, ld n, destroyed
+  void* V;             // scratch n x r, ld n
+  void* Q;             // n x n, ld n
+  void* W;             // r x r, ld r
+  int n, r;
+};
+
+struct FoldTask {      // R0 (n x n upper) of K(cand, samples)^T, streamed
+  const int* cand;     // n point indices
+  const int* samp;     // m point indices
+  double* R;           // n x n, ld n (output)
+  int n, m;
+};
+
+struct KgramTask {     // G (+)= K(cand, samp) K(cand, samp)^T
+  const int* cand;
+  const int* samp;
+  double* G;
+  int n, m, ldg;
+  int accumulate;
+};
+
+struct AsmTask {       // out(i, j) = K(x[ridx[i]], x[cidx[j]])
+  void* out;
+  const int* ridx;     // null = contiguous from r0
+  const int* cidx;     // null = contiguous from c0
+  int r0, c0, nr, nc, ld;
+};
+
+struct CopyTask {      // dst(i, j) = src(i, j) or src(j, i) (transpose)
+  const void* src;
+  void* dst;
+  int rows, cols, lds, ldd;
+};
+
+struct InterpTask {    // P (n x r) from piv, T = R11^-1 R12 (r x (n-r), ld ldt)
+  const int* piv;
+  const void* T;
+  void* P;
+  int n, r, ldt;
+};
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (defined in the k_*.cu files).  Each takes a device array
+// of tasks plus a host-side count and maxima for the grid.
+// ---------------------------------------------------------------------------
+enum class Prec { F64 = 0, F32 = 1 };
+
+void launch_gemm(Prec p, bool trA, bool trB, const GemmTask* d_tasks, const GemmTerm* d_terms,
+                 int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64 = false);
+void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s);
+void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks,
+                 int maxnrhs, cudaStream_t s);
+void launch_pchol(const CholTask* d, int ntasks, cudaStream_t s);
+void launch_pqr(const PqrTask* d, int ntasks, cudaStream_t s);
+void launch_hqr(Prec p, const HqrTask* d, int ntasks, cudaStream_t s);
+void launch_fold(const FoldTask* d, int ntasks, Points pts, KParams kp, cudaStream_t s);
+void launch_kgram(Prec p, const KgramTask* d, int ntasks, int maxn, Points pts, KParams kp,
+                  cudaStream_t s);
+void launch_assemble(Prec p, const AsmTask* d, int ntasks, int maxr, int maxc, Points pts,
+                     KParams kp, cudaStream_t s);
+void launch_copy(Prec src, Prec dst, bool transpose, const CopyTask* d, int ntasks, int maxr,
+                 int maxc, cudaStream_t s);
+void launch_interp(Prec p, const InterpTask* d, int ntasks, cudaStream_t s);
+void launch_colnorm2(const double* X, int n, int nrhs, int64_t ld, double* out, cudaStream_t s);
+void launch_axpy_cols(double* Y, const double* X, int n, int nrhs, int64_t ldy, int64_t ldx,
+                      double alpha, cudaStream_t s);
+void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int64_t* map,
+                         int64_t n, int nrhs, bool scatter, cudaStream_t s);
+void launch_fill_eye(Prec p, void* A, int n, int ld, cudaStream_t s);
+void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int k0, int k1,
+                       int col_begin, int col_end, cudaStream_t s);
+void launch_logdet_lu(const LuTask* d, int ntasks, double* out_log, double* out_sign,
+                      bool cholesky, cudaStream_t s);
+
+}  // namespace h2

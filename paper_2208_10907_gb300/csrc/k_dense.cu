@@ -1,0 +1,912 @@
+// Batched small dense linear algebra, one CTA per box (n <= 256).
+//
+// LU with partial pivoting (eq. lu), triangular solves (the eliminations of
+// S^RS and S^SR and the solve sweeps), pivoted Cholesky of a Gram matrix
+// (= column-pivoted QR of the block row, eq. u / eq. fillu), column-pivoted
+// Householder QR, Householder QR with explicit Q (orthogonalised basis
+// [U^R U^S]), the streamed fold of a far-field block row and the
+// interpolation matrix of the ID.
+#include "h2_common.cuh"
+
+namespace h2 {
+
+namespace {
+
+constexpr int NT = 256;
+
+template <typename T> __device__ __forceinline__ T tabs(T x) { return x < (T)0 ? -x : x; }
+
+// Block-wide argmax of |val| with ties broken by the lowest index.
+template <typename T>
+__device__ void block_argmax(T val, int idx, T* s_val, int* s_idx, T& out_val, int& out_idx) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T v2 = __shfl_down_sync(0xffffffffu, val, o);
+    int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+    if (v2 > val || (v2 == val && i2 < idx)) { val = v2; idx = i2; }
+  }
+  if (lane == 0) { s_val[warp] = val; s_idx[warp] = idx; }
+  __syncthreads();
+  if (warp == 0) {
+    int nw = blockDim.x >> 5;
+    val = lane < nw ? s_val[lane] : (T)-1;
+    idx = lane < nw ? s_idx[lane] : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T v2 = __shfl_down_sync(0xffffffffu, val, o);
+      int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+      if (v2 > val || (v2 == val && i2 < idx)) { val = v2; idx = i2; }
+    }
+    if (lane == 0) { s_val[0] = val; s_idx[0] = idx; }
+  }
+  __syncthreads();
+  out_val = s_val[0];
+  out_idx = s_idx[0];
+  __syncthreads();
+}
+
+template <typename T> __device__ T block_sum(T v, T* s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) s[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int nw = blockDim.x >> 5;
+    v = lane < nw ? s[lane] : (T)0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) s[0] = v;
+  }
+  __syncthreads();
+  T r = s[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// LU with partial pivoting of an m x nc panel (m >= nc), right-looking,
+// column k and row k staged in shared memory.  Ties -> lowest row index.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) getrf_kernel(const LuTask* __restrict__ tasks) {
+  const LuTask tk = tasks[blockIdx.x];
+  T* A = reinterpret_cast<T*>(tk.A);
+  const int m = tk.m, nc = tk.nc, lda = tk.lda;
+  __shared__ T s_val[32];
+  __shared__ int s_idx[32];
+  extern __shared__ unsigned char smem_raw[];
+  T* colk = reinterpret_cast<T*>(smem_raw);   // m
+  T* rowk = colk + m;                          // nc
+  bool singular = false;
+  for (int k = 0; k < nc; ++k) {
+    T best = (T)-1;
+    int bi = 0x7fffffff;
+    for (int i = k + threadIdx.x; i < m; i += NT) {
+      T v = tabs(A[i + (long long)k * lda]);
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+    T pv;
+    int p;
+    block_argmax(best, bi, s_val, s_idx, pv, p);
+    if (threadIdx.x == 0) tk.piv[k] = p;
+    if (p != k) {
+      for (int j = threadIdx.x; j < nc; j += NT) {
+        T a = A[k + (long long)j * lda];
+        A[k + (long long)j * lda] = A[p + (long long)j * lda];
+        A[p + (long long)j * lda] = a;
+      }
+    }
+    __syncthreads();
+    T akk = A[k + (long long)k * lda];
+    if (akk == (T)0) {
+      if (!singular && threadIdx.x == 0 && tk.info) atomicCAS(tk.info, 0, k + 1);
+      singular = true;
+      __syncthreads();
+      continue;
+    }
+    T inv = (T)1 / akk;
+    for (int i = k + 1 + threadIdx.x; i < m; i += NT) {
+      T v = A[i + (long long)k * lda] * inv;
+      A[i + (long long)k * lda] = v;
+      colk[i] = v;
+    }
+    for (int j = k + 1 + threadIdx.x; j < nc; j += NT) rowk[j] = A[k + (long long)j * lda];
+    __syncthreads();
+    const int rows = m - k - 1, cols = nc - k - 1;
+    const long long cnt = (long long)rows * cols;
+    for (long long e = threadIdx.x; e < cnt; e += NT) {
+      int i = k + 1 + (int)(e % rows);
+      int j = k + 1 + (int)(e / rows);
+      A[i + (long long)j * lda] -= colk[i] * rowk[j];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Left triangular solve B <- op(A)^-1 B on a 32-column chunk held in shared
+// memory; A read from global memory.  Optional row interchanges first.
+// ---------------------------------------------------------------------------
+constexpr int TS_COLS = 32;
+
+template <typename T, bool LOWER, bool UNIT, bool TRANSA>
+__global__ void __launch_bounds__(NT) trsm_kernel(const TrsmTask* __restrict__ tasks) {
+  const TrsmTask tk = tasks[blockIdx.x];
+  const int c0 = blockIdx.y * TS_COLS;
+  if (c0 >= tk.nrhs) return;
+  const int nc = min(TS_COLS, tk.nrhs - c0);
+  const int n = tk.n;
+  const T* A = reinterpret_cast<const T*>(tk.A);
+  T* B = reinterpret_cast<T*>(tk.B) + (long long)c0 * tk.ldb;
+  extern __shared__ unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);   // n x (TS_COLS+1)
+  const int LDX = TS_COLS + 1;
+  for (int e = threadIdx.x; e < n * nc; e += NT) {
+    int i = e % n, c = e / n;
+    X[i * LDX + c] = B[i + (long long)c * tk.ldb];
+  }
+  __syncthreads();
+  if (tk.piv) {
+    if (threadIdx.x < nc) {
+      int c = threadIdx.x;
+      for (int k = 0; k < n; ++k) {
+        int p = tk.piv[k];
+        if (p != k) {
+          T a = X[k * LDX + c];
+          X[k * LDX + c] = X[p * LDX + c];
+          X[p * LDX + c] = a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  auto aij = [&](int i, int j) -> T {
+    return TRANSA ? A[j + (long long)i * tk.lda] : A[i + (long long)j * tk.lda];
+  };
+  const int c = threadIdx.x % TS_COLS, r0 = threadIdx.x / TS_COLS;   // 8 row groups
+  const int RG = NT / TS_COLS;
+  if (LOWER) {
+    for (int j = 0; j < n; ++j) {
+      if (!UNIT) {
+        if (threadIdx.x < nc) X[j * LDX + threadIdx.x] /= aij(j, j);
+        __syncthreads();
+      }
+      if (c < nc) {
+        T xj = X[j * LDX + c];
+        for (int i = j + 1 + r0; i < n; i += RG) X[i * LDX + c] -= aij(i, j) * xj;
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int j = n - 1; j >= 0; --j) {
+      if (!UNIT) {
+        if (threadIdx.x < nc) X[j * LDX + threadIdx.x] /= aij(j, j);
+        __syncthreads();
+      }
+      if (c < nc) {
+        T xj = X[j * LDX + c];
+        for (int i = r0; i < j; i += RG) X[i * LDX + c] -= aij(i, j) * xj;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = threadIdx.x; e < n * nc; e += NT) {
+    int i = e % n, cc = e / n;
+    B[i + (long long)cc * tk.ldb] = X[i * LDX + cc];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pivoted Cholesky of a Gram matrix G = B B^T (FP64).  Its pivots and R are
+// those of the column-pivoted Householder QR of B^T: pivot on the largest
+// remaining diagonal of the Schur complement (ties -> lowest index); stop
+// when G_kk <= tol^2 G_11 (|R_kk| <= tol |R_11|) or at max_rank.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ tasks) {
+  const CholTask tk = tasks[blockIdx.x];
+  double* G = tk.G;
+  const int n = tk.n, ld = tk.ldg;
+  double* R = tk.R;   // ld n
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ double rowk[256];
+  for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) tk.piv[i] = i;
+  __syncthreads();
+  double d1 = 0.0;
+  int rank = min(n, tk.max_rank);
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = k + threadIdx.x; i < n; i += NT) {
+      double v = G[i + (long long)i * ld];
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+    double pv;
+    int p;
+    block_argmax(best, bi, s_val, s_idx, pv, p);
+    if (p != k) {
+      // symmetric swap of rows/cols k and p of the trailing matrix (full matrix)
+      for (int j = threadIdx.x; j < n; j += NT) {
+        double a = G[k + (long long)j * ld];
+        G[k + (long long)j * ld] = G[p + (long long)j * ld];
+        G[p + (long long)j * ld] = a;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += NT) {
+        double a = G[i + (long long)k * ld];
+        G[i + (long long)k * ld] = G[i + (long long)p * ld];
+        G[i + (long long)p * ld] = a;
+      }
+      for (int i = threadIdx.x; i < k; i += NT) {
+        double a = R[i + (long long)k * n];
+        R[i + (long long)k * n] = R[i + (long long)p * n];
+        R[i + (long long)p * n] = a;
+      }
+      if (threadIdx.x == 0) {
+        int t = tk.piv[k];
+        tk.piv[k] = tk.piv[p];
+        tk.piv[p] = t;
+      }
+      __syncthreads();
+    }
+    double gkk = G[k + (long long)k * ld];
+    if (k == 0) d1 = gkk;
+    if (k >= tk.max_rank || gkk <= tk.tol * tk.tol * d1 || gkk <= 0.0) {
+      rank = k;
+      break;
+    }
+    double rkk = sqrt(gkk);
+    for (int j = k + threadIdx.x; j < n; j += NT) {
+      double v = (j == k) ? rkk : G[k + (long long)j * ld] / rkk;
+      R[k + (long long)j * n] = v;
+      rowk[j] = v;
+    }
+    __syncthreads();
+    const int rem = n - k - 1;
+    const long long cnt = (long long)rem * rem;
+    for (long long e = threadIdx.x; e < cnt; e += NT) {
+      int i = k + 1 + (int)(e % rem);
+      int j = k + 1 + (int)(e / rem);
+      G[i + (long long)j * ld] -= rowk[i] * rowk[j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *tk.rank = rank;
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR with column pivoting (FP64) of an m x n matrix (n <= 256):
+// pivot = remaining column of largest 2-norm, recomputed at every step
+// (ties -> lowest index); stop at |R_kk| <= tol |R_11| or max_rank.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) pqr_kernel(const PqrTask* __restrict__ tasks) {
+  const PqrTask tk = tasks[blockIdx.x];
+  double* A = tk.A;
+  const int m = tk.m, n = tk.n, lda = tk.lda;
+  double* R = tk.R;
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ double nrm[256];
+  __shared__ double wv[256];
+  __shared__ double s_beta, s_r11;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = NT / 32;
+  for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) tk.piv[i] = i;
+  __syncthreads();
+  const int kmax = min(m, n);
+  int rank = min(kmax, tk.max_rank);
+  for (int k = 0; k < kmax; ++k) {
+    // column norms of A[k:, j], warp per column
+    for (int j = k + warp; j < n; j += nwarp) {
+      double s = 0.0;
+      for (int i = k + lane; i < m; i += 32) {
+        double a = A[i + (long long)j * lda];
+        s += a * a;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) nrm[j] = sqrt(s);
+    }
+    __syncthreads();
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int j = k + threadIdx.x; j < n; j += NT) {
+      double v = nrm[j];
+      if (v > best || (v == best && j < bi)) { best = v; bi = j; }
+    }
+    double pv;
+    int p;
+    block_argmax(best, bi, s_val, s_idx, pv, p);
+    if (p != k) {
+      for (int i = threadIdx.x; i < m; i += NT) {
+        double a = A[i + (long long)k * lda];
+        A[i + (long long)k * lda] = A[i + (long long)p * lda];
+        A[i + (long long)p * lda] = a;
+      }
+      for (int i = threadIdx.x; i < k; i += NT) {
+        double a = R[i + (long long)k * n];
+        R[i + (long long)k * n] = R[i + (long long)p * n];
+        R[i + (long long)p * n] = a;
+      }
+      if (threadIdx.x == 0) {
+        int t = tk.piv[k];
+        tk.piv[k] = tk.piv[p];
+        tk.piv[p] = t;
+      }
+      __syncthreads();
+    }
+    double alpha = pv;
+    if (k == 0 && threadIdx.x == 0) s_r11 = alpha;
+    __syncthreads();
+    if (k >= tk.max_rank || alpha <= tk.tol * s_r11 || alpha == 0.0) {
+      rank = k;
+      break;
+    }
+    // Householder vector in place: v = x - beta e1, normalised so H = I - 2 v v^T
+    double x0 = A[k + (long long)k * lda];
+    double beta = x0 >= 0.0 ? -alpha : alpha;
+    double v0 = x0 - beta;
+    double vnorm2 = alpha * alpha - x0 * x0 + v0 * v0;
+    double inv = 1.0 / sqrt(vnorm2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      A[k + (long long)k * lda] = v0 * inv;
+      s_beta = beta;
+    }
+    for (int i = k + 1 + threadIdx.x; i < m; i += NT) A[i + (long long)k * lda] *= inv;
+    __syncthreads();
+    // apply to trailing columns: w_j = v^T A[k:, j]
+    for (int j = k + 1 + warp; j < n; j += nwarp) {
+      double s = 0.0;
+      for (int i = k + lane; i < m; i += 32) s += A[i + (long long)k * lda] * A[i + (long long)j * lda];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      s = __shfl_sync(0xffffffffu, s, 0);
+      for (int i = k + lane; i < m; i += 32) A[i + (long long)j * lda] -= 2.0 * A[i + (long long)k * lda] * s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) R[k + (long long)k * n] = s_beta;
+    for (int j = k + 1 + threadIdx.x; j < n; j += NT) R[k + (long long)j * n] = A[k + (long long)j * lda];
+    __syncthreads();
+  }
+  (void)wv;
+  if (threadIdx.x == 0) *tk.rank = rank;
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR of M (n x r) with explicit Q: Q = [q_0 .. q_{n-1}], first r
+// columns span range(M) (U^S), the rest its complement (U^R).  Output
+// columns are ordered [U^R U^S]; W = the r x r triangular factor.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) hqr_kernel(const HqrTask* __restrict__ tasks) {
+  const HqrTask tk = tasks[blockIdx.x];
+  const int n = tk.n, r = tk.r, m = n - r;
+  T* M = reinterpret_cast<T*>(tk.M);
+  T* V = reinterpret_cast<T*>(tk.V);
+  T* Q = reinterpret_cast<T*>(tk.Q);
+  T* W = reinterpret_cast<T*>(tk.W);
+  __shared__ T s_red[32];
+  __shared__ T s_beta;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = NT / 32;
+  for (int k = 0; k < r; ++k) {
+    T s = 0;
+    for (int i = k + threadIdx.x; i < n; i += NT) {
+      T a = M[i + (long long)k * n];
+      s += a * a;
+    }
+    T alpha2 = block_sum(s, s_red);
+    T alpha = sqrt(alpha2);
+    T x0 = M[k + (long long)k * n];
+    T beta = x0 >= (T)0 ? -alpha : alpha;
+    T v0 = x0 - beta;
+    T vn2 = alpha2 - x0 * x0 + v0 * v0;
+    T inv = vn2 > (T)0 ? (T)1 / sqrt(vn2) : (T)0;
+    for (int i = threadIdx.x; i < n; i += NT) {
+      T v = (i < k) ? (T)0 : (i == k ? v0 * inv : M[i + (long long)k * n] * inv);
+      V[i + (long long)k * n] = v;
+    }
+    if (threadIdx.x == 0) s_beta = (vn2 > (T)0) ? beta : x0;
+    __syncthreads();
+    for (int j = k + 1 + warp; j < r; j += nwarp) {
+      T sj = 0;
+      for (int i = k + lane; i < n; i += 32) sj += V[i + (long long)k * n] * M[i + (long long)j * n];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sj += __shfl_down_sync(0xffffffffu, sj, o);
+      sj = __shfl_sync(0xffffffffu, sj, 0);
+      for (int i = k + lane; i < n; i += 32) M[i + (long long)j * n] -= (T)2 * V[i + (long long)k * n] * sj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) M[k + (long long)k * n] = s_beta;
+    __syncthreads();
+  }
+  // W = upper triangle of M[0:r, 0:r]
+  for (int e = threadIdx.x; e < r * r; e += NT) {
+    int i = e % r, j = e / r;
+    W[i + (long long)j * r] = (i <= j) ? M[i + (long long)j * n] : (T)0;
+  }
+  // Q = H_0 ... H_{r-1} I, written with columns permuted to [U^R U^S]:
+  // column c of the Householder Q goes to position c < r ? m + c : c - r.
+  for (int e = threadIdx.x; e < n * n; e += NT) {
+    int i = e % n, c = e / n;
+    int pos = c < r ? m + c : c - r;
+    Q[i + (long long)pos * n] = (i == c) ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  for (int k = r - 1; k >= 0; --k) {
+    for (int c = warp; c < n; c += nwarp) {
+      int pos = c < r ? m + c : c - r;
+      T* q = Q + (long long)pos * n;
+      T sj = 0;
+      for (int i = k + lane; i < n; i += 32) sj += V[i + (long long)k * n] * q[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sj += __shfl_down_sync(0xffffffffu, sj, o);
+      sj = __shfl_sync(0xffffffffu, sj, 0);
+      if (sj != (T)0)
+        for (int i = k + lane; i < n; i += 32) q[i] -= (T)2 * V[i + (long long)k * n] * sj;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Streamed fold of a far-field block row: R0 (n x n, upper) with
+// R0^T R0 = B B^T for B = K(x[cand], x[samp]) (n x m), by Householder
+// elimination of 32-sample chunks of B^T against the running triangle.
+// The chunk is evaluated straight into shared memory; B is never stored.
+// ---------------------------------------------------------------------------
+constexpr int FC = 32;
+
+__global__ void __launch_bounds__(NT) fold_kernel(const FoldTask* __restrict__ tasks, Points pts,
+                                                  KParams kp) {
+  const FoldTask tk = tasks[blockIdx.x];
+  const int n = tk.n;
+  double* R = tk.R;
+  extern __shared__ double fold_smem[];
+  double (*C)[257] = reinterpret_cast<double (*)[257]>(fold_smem);   // FC x 257
+  __shared__ double vs[FC + 1];
+  __shared__ double s_tau, s_beta;
+  __shared__ double cx[256], cy[256], cz[256];
+  __shared__ int s_skip;
+  for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    int g = tk.cand[i];
+    cx[i] = pts.x[g];
+    cy[i] = pts.y[g];
+    cz[i] = pts.z[g];
+  }
+  __syncthreads();
+  for (int s0 = 0; s0 < tk.m; s0 += FC) {
+    const int c = min(FC, tk.m - s0);
+    for (int e = threadIdx.x; e < FC * n; e += NT) {
+      int q = e / n, j = e % n;
+      double v = 0.0;
+      if (q < c) {
+        int g = tk.samp[s0 + q];
+        v = kernel_eval(kp, cx[j] - pts.x[g], cy[j] - pts.y[g], cz[j] - pts.z[g]);
+      }
+      C[q][j] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+      if (threadIdx.x < 32) {
+        double rkk = R[k + (long long)k * n];
+        double x = threadIdx.x < FC ? C[threadIdx.x][k] : 0.0;
+        double s = x * x;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        s = __shfl_sync(0xffffffffu, s, 0);
+        if (threadIdx.x == 0) {
+          if (s == 0.0) {
+            s_skip = 1;
+          } else {
+            double alpha = sqrt(rkk * rkk + s);
+            double beta = rkk >= 0.0 ? -alpha : alpha;
+            double v0 = rkk - beta;
+            s_tau = 2.0 / (v0 * v0 + s);
+            s_beta = beta;
+            vs[0] = v0;
+            s_skip = 0;
+          }
+        }
+        if (threadIdx.x < FC) vs[threadIdx.x + 1] = x;
+      }
+      __syncthreads();
+      if (!s_skip) {
+        const double tau = s_tau;
+        for (int j = k + 1 + threadIdx.x; j < n; j += NT) {
+          double rkj = R[k + (long long)j * n];
+          double w = vs[0] * rkj;
+#pragma unroll 8
+          for (int q = 0; q < FC; ++q) w += vs[q + 1] * C[q][j];
+          w *= tau;
+          R[k + (long long)j * n] = rkj - vs[0] * w;
+#pragma unroll 8
+          for (int q = 0; q < FC; ++q) C[q][j] -= vs[q + 1] * w;
+        }
+        if (threadIdx.x == 0) R[k + (long long)k * n] = s_beta;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// G (+)= B B^T for B = K(x[cand], x[samp]), tiles 64 x 64, kernel values
+// generated on the fly (never stored).  Computed in T, accumulated in FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) kgram_kernel(const KgramTask* __restrict__ tasks, Points pts,
+                                                   KParams kp) {
+  const KgramTask tk = tasks[blockIdx.x];
+  const int tiles = (tk.n + 63) / 64;
+  if ((int)blockIdx.y >= tiles * tiles) return;
+  const int i0 = (blockIdx.y % tiles) * 64, j0 = (blockIdx.y / tiles) * 64;
+  __shared__ T As[16][68];
+  __shared__ T Bs[16][68];
+  __shared__ double ax[64], ay[64], az[64], bx[64], by[64], bz[64];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  if (tid < 64) {
+    int i = i0 + tid;
+    int g = i < tk.n ? tk.cand[i] : tk.cand[0];
+    ax[tid] = pts.x[g]; ay[tid] = pts.y[g]; az[tid] = pts.z[g];
+  } else if (tid < 128) {
+    int j = j0 + tid - 64;
+    int g = j < tk.n ? tk.cand[j] : tk.cand[0];
+    bx[tid - 64] = pts.x[g]; by[tid - 64] = pts.y[g]; bz[tid - 64] = pts.z[g];
+  }
+  __syncthreads();
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+  for (int k0 = 0; k0 < tk.m; k0 += 16) {
+    {
+      int i = tid % 64, kk = tid / 64;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int k = kk + 4 * q;
+        int gk = k0 + k;
+        T va = (T)0, vb = (T)0;
+        if (gk < tk.m) {
+          int g = tk.samp[gk];
+          double sx = pts.x[g], sy = pts.y[g], sz = pts.z[g];
+          if (i0 + i < tk.n) va = KEval<T>::eval(kp, ax[i] - sx, ay[i] - sy, az[i] - sz);
+          if (j0 + i < tk.n) vb = KEval<T>::eval(kp, bx[i] - sx, by[i] - sy, bz[i] - sz);
+        }
+        As[k][i] = va;
+        Bs[k][i] = vb;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[k][ty + 16 * q];
+        b[q] = Bs[k][tx + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int gi = i0 + ty + 16 * p;
+    if (gi >= tk.n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int gj = j0 + tx + 16 * q;
+      if (gj >= tk.n) continue;
+      double v = (double)acc[p][q];
+      long long o = gi + (long long)gj * tk.ldg;
+      tk.G[o] = tk.accumulate ? tk.G[o] + v : v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel-block assembly: out(i, j) = K(x[ridx[i]], x[cidx[j]]).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) assemble_kernel(const AsmTask* __restrict__ tasks, Points pts,
+                                                      KParams kp) {
+  const AsmTask tk = tasks[blockIdx.x];
+  const int j = blockIdx.y;
+  if (j >= tk.nc) return;
+  const int gj = tk.cidx ? tk.cidx[j] : tk.c0 + j;
+  const double xj = pts.x[gj], yj = pts.y[gj], zj = pts.z[gj];
+  T* out = reinterpret_cast<T*>(tk.out) + (long long)j * tk.ld;
+  for (int i = threadIdx.x; i < tk.nr; i += NT) {
+    int gi = tk.ridx ? tk.ridx[i] : tk.r0 + i;
+    out[i] = KEval<T>::eval(kp, pts.x[gi] - xj, pts.y[gi] - yj, pts.z[gi] - zj);
+  }
+}
+
+template <typename TS, typename TD, bool TR>
+__global__ void __launch_bounds__(NT) copy_kernel(const CopyTask* __restrict__ tasks) {
+  const CopyTask tk = tasks[blockIdx.x];
+  const TS* s = reinterpret_cast<const TS*>(tk.src);
+  TD* d = reinterpret_cast<TD*>(tk.dst);
+  const long long cnt = (long long)tk.rows * tk.cols;
+  for (long long e = (long long)blockIdx.y * NT + threadIdx.x; e < cnt; e += (long long)gridDim.y * NT) {
+    int i = (int)(e % tk.rows), j = (int)(e / tk.rows);
+    TS v = TR ? s[j + (long long)i * tk.lds] : s[i + (long long)j * tk.lds];
+    d[i + (long long)j * tk.ldd] = (TD)v;
+  }
+}
+
+// P (n x r): P[piv[i], i] = 1 (i < r); P[piv[c], :] = T[:, c - r]^T (c >= r).
+template <typename T>
+__global__ void __launch_bounds__(NT) interp_kernel(const InterpTask* __restrict__ tasks) {
+  const InterpTask tk = tasks[blockIdx.x];
+  T* P = reinterpret_cast<T*>(tk.P);
+  const T* Tm = reinterpret_cast<const T*>(tk.T);
+  const int n = tk.n, r = tk.r;
+  for (long long e = threadIdx.x; e < (long long)n * r; e += NT) {
+    int c = (int)(e % n), j = (int)(e / n);
+    int row = tk.piv[c];
+    T v;
+    if (c < r) v = (c == j) ? (T)1 : (T)0;
+    else v = Tm[j + (long long)(c - r) * tk.ldt];
+    P[row + (long long)j * n] = v;
+  }
+}
+
+__global__ void colnorm2_kernel(const double* X, int n, int nrhs, long long ld, double* out) {
+  __shared__ double s[32];
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    double v = X[i + (long long)c * ld];
+    acc += v * v;
+  }
+  double t = block_sum(acc, s);
+  if (threadIdx.x == 0) out[c] = t;
+}
+
+__global__ void axpy_cols_kernel(double* Y, const double* X, int n, int nrhs, long long ldy, long long ldx,
+                                 double alpha) {
+  long long cnt = (long long)n * nrhs;
+  for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < cnt; e += (long long)gridDim.x * NT) {
+    int i = (int)(e % n), c = (int)(e / n);
+    Y[i + c * ldy] += alpha * X[i + c * ldx];
+  }
+}
+
+__global__ void permute_rows_kernel(const double* src, long long lds, double* dst, long long ldd,
+                                    const int64_t* map, long long n, int nrhs, bool scatter) {
+  long long cnt = n * nrhs;
+  for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < cnt; e += (long long)gridDim.x * NT) {
+    long long i = e % n;
+    int c = (int)(e / n);
+    if (scatter) dst[map[i] + c * ldd] = src[i + c * lds];
+    else dst[i + c * ldd] = src[map[i] + c * lds];
+  }
+}
+
+template <typename T> __global__ void eye_kernel(T* A, int n, int ld) {
+  long long cnt = (long long)n * n;
+  for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < cnt; e += (long long)gridDim.x * NT) {
+    int i = (int)(e % n), j = (int)(e / n);
+    A[i + (long long)j * ld] = (i == j) ? (T)1 : (T)0;
+  }
+}
+
+// Apply row interchanges piv[k0..k1) to columns [cb, ce) of A.
+template <typename T>
+__global__ void laswp_kernel(T* A, int lda, const int* piv, int k0, int k1, int cb, int ce) {
+  for (int j = cb + blockIdx.x * NT + threadIdx.x; j < ce; j += gridDim.x * NT) {
+    T* col = A + (long long)j * lda;
+    for (int k = k0; k < k1; ++k) {
+      int p = piv[k];
+      if (p != k) {
+        T a = col[k];
+        col[k] = col[p];
+        col[p] = a;
+      }
+    }
+  }
+}
+
+// log|det| and sign of LU (or Cholesky: 2 sum log L_kk) factors, one CTA
+// per factored block; results per task.
+__global__ void logdet_kernel(const LuTask* __restrict__ tasks, double* out_log, double* out_sign,
+                              bool chol) {
+  const LuTask tk = tasks[blockIdx.x];
+  __shared__ double s[32];
+  const double* A = reinterpret_cast<const double*>(tk.A);
+  double acc = 0.0, neg = 0.0;
+  for (int k = threadIdx.x; k < tk.nc; k += NT) {
+    double d = A[k + (long long)k * tk.lda];
+    acc += log(fabs(d));
+    if (!chol) {
+      if (d < 0.0) neg += 1.0;
+      if (tk.piv[k] != k) neg += 1.0;
+    }
+  }
+  double t = block_sum(acc, s);
+  double ng = block_sum(neg, s);
+  if (threadIdx.x == 0) {
+    out_log[blockIdx.x] = chol ? 2.0 * t : t;
+    out_sign[blockIdx.x] = (fmod(ng, 2.0) == 0.0) ? 1.0 : -1.0;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers ----
+void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  // panel rows up to a few thousand (root panels): smem = (m + nc) * sizeof(T)
+  // is sized by the caller's maximum via the attribute below.
+  size_t smem = (size_t)(8192 + 256) * (p == Prec::F64 ? 8 : 4);
+  if (p == Prec::F64) {
+    H2_CUDA(cudaFuncSetAttribute(getrf_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    getrf_kernel<double><<<ntasks, NT, smem, s>>>(d);
+  } else {
+    H2_CUDA(cudaFuncSetAttribute(getrf_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    getrf_kernel<float><<<ntasks, NT, smem, s>>>(d);
+  }
+  H2_LAUNCH_CHECK();
+}
+
+template <typename T>
+static void trsm_dispatch(bool lower, bool unit, bool transA, const TrsmTask* d, dim3 grid, size_t smem,
+                          cudaStream_t s) {
+#define H2_TRSM_CASE(L, U, TR)                                                                        \
+  if (lower == L && unit == U && transA == TR) {                                                      \
+    H2_CUDA(cudaFuncSetAttribute(trsm_kernel<T, L, U, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem));                                                         \
+    trsm_kernel<T, L, U, TR><<<grid, NT, smem, s>>>(d);                                               \
+    return;                                                                                           \
+  }
+  H2_TRSM_CASE(true, true, false)
+  H2_TRSM_CASE(true, false, false)
+  H2_TRSM_CASE(false, false, false)
+  H2_TRSM_CASE(false, true, false)
+  H2_TRSM_CASE(true, false, true)
+  H2_TRSM_CASE(false, false, true)
+  H2_TRSM_CASE(true, true, true)
+  H2_TRSM_CASE(false, true, true)
+#undef H2_TRSM_CASE
+}
+
+void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks, int maxnrhs,
+                 cudaStream_t s) {
+  if (ntasks <= 0 || maxnrhs <= 0) return;
+  dim3 grid(ntasks, (maxnrhs + TS_COLS - 1) / TS_COLS);
+  size_t smem = (size_t)256 * (TS_COLS + 1) * (p == Prec::F64 ? 8 : 4);
+  if (p == Prec::F64) trsm_dispatch<double>(lower, unit, transA, d, grid, smem, s);
+  else trsm_dispatch<float>(lower, unit, transA, d, grid, smem, s);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_pchol(const CholTask* d, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  pchol_kernel<<<ntasks, NT, 0, s>>>(d);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_pqr(const PqrTask* d, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  pqr_kernel<<<ntasks, NT, 0, s>>>(d);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_hqr(Prec p, const HqrTask* d, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  if (p == Prec::F64) hqr_kernel<double><<<ntasks, NT, 0, s>>>(d);
+  else hqr_kernel<float><<<ntasks, NT, 0, s>>>(d);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_fold(const FoldTask* d, int ntasks, Points pts, KParams kp, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  size_t smem = (size_t)FC * 257 * sizeof(double);
+  H2_CUDA(cudaFuncSetAttribute(fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  fold_kernel<<<ntasks, NT, smem, s>>>(d, pts, kp);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_kgram(Prec p, const KgramTask* d, int ntasks, int maxn, Points pts, KParams kp, cudaStream_t s) {
+  if (ntasks <= 0 || maxn <= 0) return;
+  int t = (maxn + 63) / 64;
+  dim3 grid(ntasks, t * t);
+  if (p == Prec::F64) kgram_kernel<double><<<grid, NT, 0, s>>>(d, pts, kp);
+  else kgram_kernel<float><<<grid, NT, 0, s>>>(d, pts, kp);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_assemble(Prec p, const AsmTask* d, int ntasks, int maxr, int maxc, Points pts, KParams kp,
+                     cudaStream_t s) {
+  if (ntasks <= 0 || maxc <= 0) return;
+  dim3 grid(ntasks, maxc);
+  if (p == Prec::F64) assemble_kernel<double><<<grid, NT, 0, s>>>(d, pts, kp);
+  else assemble_kernel<float><<<grid, NT, 0, s>>>(d, pts, kp);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_copy(Prec src, Prec dst, bool transpose, const CopyTask* d, int ntasks, int maxr, int maxc,
+                 cudaStream_t s) {
+  if (ntasks <= 0) return;
+  long long cnt = (long long)maxr * maxc;
+  int gy = (int)std::min<long long>(64, (cnt + NT - 1) / NT);
+  if (gy < 1) gy = 1;
+  dim3 grid(ntasks, gy);
+#define H2_COPY(TS, TD)                                                  \
+  if (transpose) copy_kernel<TS, TD, true><<<grid, NT, 0, s>>>(d);      \
+  else copy_kernel<TS, TD, false><<<grid, NT, 0, s>>>(d);
+  if (src == Prec::F64 && dst == Prec::F64) { H2_COPY(double, double) }
+  else if (src == Prec::F64 && dst == Prec::F32) { H2_COPY(double, float) }
+  else if (src == Prec::F32 && dst == Prec::F64) { H2_COPY(float, double) }
+  else { H2_COPY(float, float) }
+#undef H2_COPY
+  H2_LAUNCH_CHECK();
+}
+
+void launch_interp(Prec p, const InterpTask* d, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  if (p == Prec::F64) interp_kernel<double><<<ntasks, NT, 0, s>>>(d);
+  else interp_kernel<float><<<ntasks, NT, 0, s>>>(d);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_colnorm2(const double* X, int n, int nrhs, int64_t ld, double* out, cudaStream_t s) {
+  if (nrhs <= 0) return;
+  colnorm2_kernel<<<nrhs, NT, 0, s>>>(X, n, nrhs, ld, out);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_axpy_cols(double* Y, const double* X, int n, int nrhs, int64_t ldy, int64_t ldx, double alpha,
+                      cudaStream_t s) {
+  long long cnt = (long long)n * nrhs;
+  if (cnt <= 0) return;
+  int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
+  axpy_cols_kernel<<<g, NT, 0, s>>>(Y, X, n, nrhs, ldy, ldx, alpha);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int64_t* map,
+                         int64_t n, int nrhs, bool scatter, cudaStream_t s) {
+  long long cnt = (long long)n * nrhs;
+  if (cnt <= 0) return;
+  int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
+  permute_rows_kernel<<<g, NT, 0, s>>>(src, lds, dst, ldd, map, n, nrhs, scatter);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_fill_eye(Prec p, void* A, int n, int ld, cudaStream_t s) {
+  long long cnt = (long long)n * n;
+  int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
+  if (p == Prec::F64) eye_kernel<double><<<g, NT, 0, s>>>((double*)A, n, ld);
+  else eye_kernel<float><<<g, NT, 0, s>>>((float*)A, n, ld);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int k0, int k1, int cb, int ce,
+                       cudaStream_t s) {
+  (void)ncols;
+  if (ce <= cb || k1 <= k0) return;
+  int g = std::min(152 * 4, (ce - cb + NT - 1) / NT);
+  if (p == Prec::F64) laswp_kernel<double><<<g, NT, 0, s>>>((double*)A, lda, piv, k0, k1, cb, ce);
+  else laswp_kernel<float><<<g, NT, 0, s>>>((float*)A, lda, piv, k0, k1, cb, ce);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_logdet_lu(const LuTask* d, int ntasks, double* out_log, double* out_sign, bool cholesky,
+                      cudaStream_t s) {
+  if (ntasks <= 0) return;
+  logdet_kernel<<<ntasks, NT, 0, s>>>(d, out_log, out_sign, cholesky);
+  H2_LAUNCH_CHECK();
+}
+
+}  // namespace h2

@@ -1,0 +1,137 @@
+// Batched, segmented SIMT GEMM: C = alpha * sum_t op(A_t) op(B_t) + beta * Cin.
+//
+// Every task owns one output matrix; the terms of a task are summed in the
+// CTA's registers (owner-computes, deterministic, no atomics).  This one
+// kernel serves the fill-in Grams (sum over near boxes), the projections
+// (eq. rs, eq. ss), the Schur updates, the near-field part of the H^2
+// matvec and the solve sweeps.
+#include "h2_common.cuh"
+
+namespace h2 {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <typename T> __device__ __forceinline__ T ld_elem(const void* p, long long idx, bool f64in) {
+  if (f64in) return (T)(reinterpret_cast<const double*>(p)[idx]);
+  return reinterpret_cast<const T*>(p)[idx];
+}
+
+template <typename T, bool TRA, bool TRB, bool F64IN>
+__global__ void __launch_bounds__(NT) gemm_kernel(const GemmTask* __restrict__ tasks,
+                                                  const GemmTerm* __restrict__ terms) {
+  const GemmTask tk = tasks[blockIdx.x];
+  const int tiles_m = (tk.M + BM - 1) / BM;
+  const int tiles_n = (tk.N + BN - 1) / BN;
+  const int tile = blockIdx.y;
+  if (tile >= tiles_m * tiles_n) return;
+  const int i0 = (tile % tiles_m) * BM;
+  const int j0 = (tile / tiles_m) * BN;
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+
+  for (int t = tk.t0; t < tk.t0 + tk.nt; ++t) {
+    const GemmTerm tm = terms[t];
+    for (int k0 = 0; k0 < tm.K; k0 += BK) {
+      // ---- stage op(A) tile (BM x BK) as As[k][i]
+      if (!TRA) {
+        int i = tid % 64, kk = tid / 64;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int k = kk + 4 * q;
+          int gi = i0 + i, gk = k0 + k;
+          As[k][i] = (gi < tk.M && gk < tm.K) ? ld_elem<T>(tm.A, (long long)gi + (long long)gk * tm.lda, F64IN) : (T)0;
+        }
+      } else {
+        int k = tid % 16, ii = tid / 16;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int i = ii + 16 * q;
+          int gi = i0 + i, gk = k0 + k;
+          As[k][i] = (gi < tk.M && gk < tm.K) ? ld_elem<T>(tm.A, (long long)gk + (long long)gi * tm.lda, F64IN) : (T)0;
+        }
+      }
+      // ---- stage op(B) tile (BK x BN) as Bs[k][j]
+      if (!TRB) {
+        int k = tid % 16, jj = tid / 16;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int j = jj + 16 * q;
+          int gj = j0 + j, gk = k0 + k;
+          Bs[k][j] = (gj < tk.N && gk < tm.K) ? ld_elem<T>(tm.B, (long long)gk + (long long)gj * tm.ldb, F64IN) : (T)0;
+        }
+      } else {
+        int j = tid % 64, kk = tid / 64;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int k = kk + 4 * q;
+          int gj = j0 + j, gk = k0 + k;
+          Bs[k][j] = (gj < tk.N && gk < tm.K) ? ld_elem<T>(tm.B, (long long)gj + (long long)gk * tm.ldb, F64IN) : (T)0;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        T a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a[q] = As[k][ty + 16 * q];
+          b[q] = Bs[k][tx + 16 * q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+      }
+      __syncthreads();
+    }
+  }
+  T* C = reinterpret_cast<T*>(tk.C);
+  const T* Cin = reinterpret_cast<const T*>(tk.Cin);
+  const T alpha = (T)tk.alpha, beta = (T)tk.beta;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int gi = i0 + ty + 16 * p;
+    if (gi >= tk.M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int gj = j0 + tx + 16 * q;
+      if (gj >= tk.N) continue;
+      T v = alpha * acc[p][q];
+      if (Cin != nullptr && tk.beta != 0.0) v += beta * Cin[gi + (long long)gj * tk.ldcin];
+      C[gi + (long long)gj * tk.ldc] = v;
+    }
+  }
+}
+
+template <typename T, bool F64IN>
+void dispatch(bool trA, bool trB, const GemmTask* d_tasks, const GemmTerm* d_terms, int ntasks,
+              dim3 grid, cudaStream_t s) {
+  if (!trA && !trB) gemm_kernel<T, false, false, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
+  else if (!trA && trB) gemm_kernel<T, false, true, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
+  else if (trA && !trB) gemm_kernel<T, true, false, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
+  else gemm_kernel<T, true, true, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
+}
+
+}  // namespace
+
+void launch_gemm(Prec p, bool trA, bool trB, const GemmTask* d_tasks, const GemmTerm* d_terms,
+                 int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64) {
+  if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return;
+  int tiles = ((maxM + BM - 1) / BM) * ((maxN + BN - 1) / BN);
+  dim3 grid(ntasks, tiles);
+  if (p == Prec::F64) dispatch<double, false>(trA, trB, d_tasks, d_terms, ntasks, grid, s);
+  else if (inputs_f64) dispatch<float, true>(trA, trB, d_tasks, d_terms, ntasks, grid, s);
+  else dispatch<float, false>(trA, trB, d_tasks, d_terms, ntasks, grid, s);
+  H2_LAUNCH_CHECK();
+}
+
+}  // namespace h2

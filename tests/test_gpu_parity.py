@@ -1,0 +1,120 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.  Solutions after refinement are compared (pivot choices
+may differ, so factors are not); the H^2 matvec and the log-determinant are
+compared directly."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import h2ulv_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2208_10907_gb300 import h2ulv as H  # noqa: E402
+
+CASES = {
+    # name: (points, kernel, leaf, tol, max_rank)
+    "sphereball4k_yukawa": (lambda: synth.sphere_ball(4096, 21), "yukawa", 128, 1e-10, 128),
+    "surfaces8k_laplace": (lambda: synth.surface_union(8192, 4), "laplace", 128, 1e-6, 128),
+    "ragged3000": (lambda: synth.sphere_ball(3000, 5), "laplace", 100, 1e-8, 64),
+    "cube4k_dense": (lambda: synth.cube(4096, 0), "laplace", 256, 1e-8, 128),
+    "tiny100": (lambda: synth.cube(100, 9), "laplace", 256, 1e-8, 128),
+}
+
+_cache = {}
+
+
+def oracle_case(name):
+    if name not in _cache:
+        mk, kern, leaf, tol, mr = CASES[name]
+        X = mk()
+        pb = O.Problem(X, kern, leaf, 1.0, tol, mr)
+        _cache[name] = (X, pb, O.H2Operator(pb), O.ULVFactor(pb))
+    return _cache[name]
+
+
+def gpu_handle(X, kern, leaf, tol, mr):
+    pts = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    return H.h2_construct(pts, len(X), H.make_kernel(kern), H.make_options(leaf=leaf, tol=tol, max_rank=mr))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_matvec_matches_oracle_operator(name):
+    X, pb, op, _ = oracle_case(name)
+    _, kern, leaf, tol, mr = CASES[name]
+    h = gpu_handle(X, kern, leaf, tol, mr)
+    try:
+        N = len(X)
+        xs = synth.rhs(N, 3, 11)
+        x = torch.from_numpy(np.ascontiguousarray(xs.T)).cuda()
+        y = torch.zeros_like(x)
+        H.h2_matvec(h, x, y, 3, N)
+        yg = y.cpu().numpy().T
+        yo = op.matvec(xs)
+        err = np.linalg.norm(yg - yo) / np.linalg.norm(yo)
+        assert err < 1e-11, err
+    finally:
+        H.h2_destroy(h)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision", [H.H2_FP64, H.H2_MIXED])
+def test_refined_solution_matches_oracle(name, precision):
+    X, pb, op, fac = oracle_case(name)
+    _, kern, leaf, tol, mr = CASES[name]
+    N = len(X)
+    b = synth.rhs(N, 1, 3)[:, 0].copy()
+    xo, relo, ito = O.refine(op, fac, b, 1e-10, 30)
+    h = gpu_handle(X, kern, leaf, tol, mr)
+    try:
+        H.h2_factor(h, precision)
+        bt = torch.from_numpy(b).cuda()
+        xt = torch.zeros_like(bt)
+        st, ach, it = H.h2_solve(h, bt, xt, 1, N, 1e-10, 30)
+        assert st == H.H2_OK, (st, ach, it)
+        assert ach[0] <= 1e-10
+        err = np.linalg.norm(xt.cpu().numpy() - xo) / np.linalg.norm(xo)
+        bound = 1e-8 if precision == H.H2_FP64 else 10 * tol
+        assert err <= max(bound, 1e-8), err
+        if precision == H.H2_FP64:
+            assert it <= ito + 1
+    finally:
+        H.h2_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["sphereball4k_yukawa", "cube4k_dense", "tiny100"])
+def test_logdet_matches_oracle(name):
+    X, pb, op, fac = oracle_case(name)
+    _, kern, leaf, tol, mr = CASES[name]
+    h = gpu_handle(X, kern, leaf, tol, mr)
+    try:
+        H.h2_factor(h, H.H2_FP64)
+        ld, sg = H.h2_logdet(h)
+        lo, so = fac.logdet()
+        assert sg[0] == so
+        assert abs(ld[0] - lo) <= 1e-9 * abs(lo), (ld[0], lo)
+    finally:
+        H.h2_destroy(h)
+
+
+def test_host_buffers_multiple_rhs():
+    X, pb, op, fac = oracle_case("ragged3000")
+    _, kern, leaf, tol, mr = CASES["ragged3000"]
+    N = len(X)
+    B = synth.rhs(N, 4, 8)
+    Bc = np.ascontiguousarray(B.T)          # column-major N x 4, host
+    Xc = np.zeros_like(Bc)
+    h = H.h2_construct(np.ascontiguousarray(X), N, H.make_kernel(kern), H.make_options(leaf=leaf, tol=tol, max_rank=mr))
+    try:
+        H.h2_factor(h, H.H2_FP64)
+        st, ach, it = H.h2_solve(h, Bc, Xc, 4, N, 1e-10, 30)
+        assert st == H.H2_OK and np.all(ach <= 1e-10)
+        xo, _, _ = O.refine(op, fac, B, 1e-10, 30)
+        err = np.linalg.norm(Xc.T - xo) / np.linalg.norm(xo)
+        assert err <= 1e-8, err
+    finally:
+        H.h2_destroy(h)
