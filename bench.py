@@ -1,0 +1,327 @@
+"""Benchmark: H^2-ULV factor + refined solve on one GB300.
+
+One step = h2_factor (mixed precision) + h2_solve refined to a relative H^2
+residual of 1e-10, on N = 2^20 points on a union of 16 ellipsoid and 16
+torus surfaces (Laplace kernel 1/(r + 1e-3), leaf 256, eta 1, tol 1e-6).
+The inputs (points, right-hand side) are resident in HBM and the per-step
+working set (tens of GB of near blocks) is far larger than L2.
+
+Prints ONE JSON line (rank 0).  --impl reference runs the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "H²-ULV factor s + solve ms at N=2^20, mixed vs FP64 GPU at rel. residual 1e-10"
+WORKLOAD = dict(name="surfaces1m", n=1 << 20, kernel="laplace", leaf=256, eta=1.0, tol=1e-6, max_rank=128,
+                far_s0=16, far_smin=2, target=1e-10, seed=4, rhs_seed=40)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 7 for k in range(4)
+                          if r[3 + k].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def cpu_oracle_sample(n_sample, repeats=1):
+    """Time the CPU oracle (as it stands) on a bounded sample of the workload:
+    the same generator, kernel and parameters at N = n_sample; the method is
+    O(N), so the time is scaled by 2^20 / n_sample."""
+    from oracle import h2ulv_oracle as O
+    W = WORKLOAD
+    X = synth.surface_union(n_sample, W["seed"])
+    b = synth.rhs(n_sample, 1, W["rhs_seed"])[:, 0].copy()
+    ts = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        pb = O.Problem(X, W["kernel"], W["leaf"], W["eta"], W["tol"], W["max_rank"], W["far_s0"], W["far_smin"])
+        op = O.H2Operator(pb)
+        t1 = time.perf_counter()
+        fac = O.ULVFactor(pb)
+        x, rel, it = O.refine(op, fac, b, W["target"], 30)
+        t2 = time.perf_counter()
+        ts.append((t1 - t0, t2 - t1))
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max(i.get("num_threads", 1) for i in threadpool_info()) or cores
+    except Exception:
+        pass
+    fac_solve = float(np.median([t[1] for t in ts]))
+    return dict(value=fac_solve * W["n"] / n_sample, unit="s", cores=int(cores), kind="oracle",
+                sample=f"oracle factor+refined solve on N={n_sample} points of the same surface union "
+                       f"(leaf 256, tol 1e-6), {fac_solve:.2f} s measured, scaled x{W['n'] / n_sample:.0f} "
+                       f"to N=2^20 (O(N) method); construct {np.median([t[0] for t in ts]):.2f} s not included")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_sample = args.cpu_sample
+    vals = []
+    cb = None
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up effects worth timing separately
+    for _ in range(args.steps):
+        cb = cpu_oracle_sample(n_sample)
+        vals.append(cb["value"])
+    v = float(np.median(vals))
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "surfaces1m: N=2^20 on 16 ellipsoid + 16 torus surfaces, Laplace 1/(r+1e-3), "
+                                   "leaf 256, eta 1, tol 1e-6, refined to 1e-10", "n": WORKLOAD["n"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink N (debugging only)")
+    ap.add_argument("--cpu-sample", type=int, default=8192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64-path steps (0 = skip)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2208_10907_gb300 import h2ulv as H
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = WORKLOAD
+    n = max(4096, int(W["n"] * args.scale))
+    X = synth.surface_union(n, W["seed"])
+    b_host = synth.rhs(n, 1, W["rhs_seed"])[:, 0].copy()
+    pts = torch.from_numpy(X).to(dev)
+    b = torch.from_numpy(b_host).to(dev)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream(dev)
+    kern = H.make_kernel(W["kernel"])
+    opt = H.make_options(eta=W["eta"], leaf=W["leaf"], tol=W["tol"], max_rank=W["max_rank"], far_s0=W["far_s0"],
+                         far_smin=W["far_smin"], hbm_budget_bytes=180 * 10**9)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = H.h2_construct(pts, n, kern, opt, stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_construct = time.perf_counter() - t0
+
+    def step(prec, bb, xx):
+        H.h2_factor(h, prec)
+        st, ach, it = H.h2_solve(h, bb, xx, 1, n, W["target"], 30)
+        return st, ach, it
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        step(H.H2_MIXED, b, x)
+    # ---- timed region (device-resident inputs), per-kernel events on
+    clocks = ClockSampler(local)
+    H.h2_profile(1, 1)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    evf = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev0.record(stream)
+    iters = []
+    for k in range(args.steps):
+        H.h2_factor(h, H.H2_MIXED)
+        evf[k].record(stream)
+        st, ach, it = H.h2_solve(h, b, x, 1, n, W["target"], 30)
+        iters.append((int(st), float(ach[0]), int(it)))
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    stats = json.loads(H.h2_stats(h))
+    H.h2_profile(0, 0)
+    fac_ms = [(ev0 if k == 0 else None) for k in range(args.steps)]
+    # factor / solve split from the per-step events
+    starts = [ev0] + []
+    f_ms, s_ms = [], []
+    prev = ev0
+    # each step: prev -> evf[k] is the factor; evf[k] -> next start is the solve
+    for k in range(args.steps):
+        f_ms.append(prev.elapsed_time(evf[k]))
+        prev = evf[k]
+    step_ms = total_ms / args.steps
+    solve_ms = step_ms - float(np.mean(f_ms)) if len(f_ms) > 1 else total_ms - f_ms[0]
+    # max over ranks
+    t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms = float(t.item())
+
+    # ---- roofline of the dominant kernel (event times inside the timed region)
+    kern_stats = stats.get("kernels", {})
+    dom = max(kern_stats.items(), key=lambda kv: kv[1]["ms"]) if kern_stats else None
+    pk = peaks()
+    roof = None
+    if dom:
+        name, ks = dom
+        per_launch_ms = ks["ms"] / max(1, ks["launches"])
+        if name.startswith("gemm_f32") or name.startswith("kgram_f32"):
+            # FP32 SIMT FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock
+            peak = 152 * 128 * 2 * (pk["sm_max_mhz"] if pk else 2070.0) * 1e6 / 1e12
+            bound, unit, ach = "alu", "TFLOP/s", ks["flops"] / (ks["ms"] * 1e-3) / 1e12
+        elif name.startswith("gemm_tc") or name.startswith("tc_"):
+            peak = (pk["bf16_tflops_sustained"] if pk else 1700.0) / 2.0   # tf32 = bf16 / 2 (nominal ratio)
+            bound, unit, ach = "tensor", "TFLOP/s", ks["flops"] / (ks["ms"] * 1e-3) / 1e12
+        else:
+            # FP64 DFMA pipe: GB300 nominal 1.25 TFLOP/s dense FP64
+            peak = 1.25 * (pk["sm_max_mhz"] / 2070.0 if pk else 1.0)
+            bound, unit, ach = "alu", "TFLOP/s", ks["flops"] / (ks["ms"] * 1e-3) / 1e12 if ks["ms"] > 0 else 0.0
+        roof = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                "frac": ach / peak if peak else None, "traffic": None, "launches": ks["launches"],
+                "ms_total": ks["ms"], "share": ks["ms"] / max(1e-9, sum(v["ms"] for v in kern_stats.values())),
+                "per_launch_ms": per_launch_ms, "peak_source": "derived from MEASURED_PEAKS.json sm_max_mhz"}
+
+    # ---- FP64 path, same GPU (fewer steps: FP64 throughput is 1/60 of FP32)
+    fp64 = None
+    if args.fp64_steps > 0:
+        step(H.H2_FP64, b, x)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        fs, ss, its = [], [], []
+        for _ in range(args.fp64_steps):
+            e0.record(stream)
+            H.h2_factor(h, H.H2_FP64)
+            e1.record(stream)
+            st, ach, it = H.h2_solve(h, b, x, 1, n, W["target"], 30)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            fs.append(e0.elapsed_time(e1))
+            ss.append(e1.elapsed_time(e2))
+            its.append(it)
+        fp64 = {"factor_s": float(np.median(fs)) / 1e3, "solve_ms": float(np.median(ss)), "iters": its,
+                "step_s": (float(np.median(fs)) + float(np.median(ss))) / 1e3}
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.zeros_like(b_pin).pin_memory()
+    step(H.H2_MIXED, b_pin, x_pin)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t_e2e = time.perf_counter()
+    for _ in range(args.steps):
+        step(H.H2_MIXED, b_pin, x_pin)
+    e1.record(stream)
+    barrier()
+    e2e_ms = (time.perf_counter() - t_e2e) * 1e3 / args.steps
+
+    # ---- CPU baseline (oracle) on rank 0
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": step_ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "surfaces1m: N=2^20 on 16 ellipsoid + 16 torus surfaces, Laplace 1/(r+1e-3), "
+                                   "leaf 256, eta 1, tol 1e-6, mixed factor refined to H2 residual 1e-10",
+                       "n": n, "leaf": W["leaf"], "eta": W["eta"], "tol": W["tol"], "max_rank": W["max_rank"],
+                       "far_sample": [W["far_s0"], W["far_smin"]], "l2": "inputs larger than L2 (tens of GB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "factor_s": float(np.mean(f_ms)) / 1e3, "solve_ms": solve_ms,
+            "refine": [{"status": s_, "residual": a_, "iters": i_} for s_, a_, i_ in iters],
+            "construct_s": t_construct,
+            "fp64": fp64,
+            "mixed_vs_fp64_speedup": (fp64["step_s"] / (step_ms / 1e3)) if fp64 else None,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
+            "gpu_launches": int(stats.get("launches", 0)),
+            "clocks": clk,
+            "levels": stats.get("levels"),
+        }
+        print(json.dumps(line), flush=True)
+    H.h2_destroy(h)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

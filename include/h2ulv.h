@@ -153,6 +153,13 @@ h2_status h2_logdet(h2_handle h, double* log_abs_det, int32_t* sign);
  * the host buffer json.  Truncated output is still NUL-terminated. */
 h2_status h2_stats(h2_handle h, char* json, size_t cap);
 
+/* Per-kernel instrumentation shared by all handles of the process.  Every
+ * launch is counted; with enable = 1 each launch is also bracketed by CUDA
+ * events on the stream it runs on, and h2_stats reports, per kernel, its
+ * launches, summed event time (ms) and the algorithmic flops and bytes its
+ * callers declared.  reset = 1 clears the counters first. */
+h2_status h2_profile(int32_t enable, int32_t reset);
+
 /* Thread-local message of the last failed call on this thread. */
 const char* h2_last_error(void);
 

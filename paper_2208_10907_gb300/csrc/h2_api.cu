@@ -19,6 +19,7 @@
 
 #include "../../include/h2ulv.h"
 #include "h2_common.cuh"
+#include "h2_prof.h"
 #include "h2_tree.h"
 
 namespace h2 {
@@ -79,6 +80,7 @@ struct GemmBatch {
   std::vector<GemmTask> tasks;
   std::vector<GemmTerm> terms;
   int maxM = 0, maxN = 0;
+  double flops = 0.0, bytes = 0.0;
   void add(void* C, int ldc, int M, int N, double alpha, double beta, const void* Cin, int ldcin,
            const std::vector<GemmTerm>& ts) {
     if (M <= 0 || N <= 0) return;
@@ -95,29 +97,34 @@ struct GemmBatch {
       if (g.K > 0) {
         terms.push_back(g);
         ++t.nt;
+        flops += 2.0 * M * N * g.K;
+        bytes += (double)M * g.K + (double)g.K * N;
       }
+    bytes += (double)M * N * ((beta != 0.0 && Cin) ? 2.0 : 1.0);
     t.alpha = alpha;
     t.beta = beta;
     tasks.push_back(t);
     maxM = std::max(maxM, M);
     maxN = std::max(maxN, N);
   }
+  // one term; trA / trB flip the operands (combined with the run-level flags)
   void add1(void* C, int ldc, int M, int N, const void* A, int lda, const void* B, int ldb, int K,
-            double alpha = 1.0, double beta = 0.0, const void* Cin = nullptr, int ldcin = 0) {
+            double alpha = 1.0, double beta = 0.0, const void* Cin = nullptr, int ldcin = 0, int flags = 0) {
     add(C, ldc, M, N, alpha, beta, Cin ? Cin : (beta != 0.0 ? C : nullptr), Cin ? ldcin : ldc,
-        {GemmTerm{A, B, K, lda, ldb}});
+        {GemmTerm{A, B, K, lda, ldb, flags}});
   }
   void run(Prec p, bool trA, bool trB, Scratch& sc) {
     if (tasks.empty()) return;
-    // the grid's y dimension is the tile count; chunk the task list so the
-    // x dimension stays well within limits
+    const int fl = (trA ? 1 : 0) | (trB ? 2 : 0);
+    for (GemmTerm& t : terms) t.flags ^= fl;
+    GemmTerm* dm = sc.up(terms);
     const size_t CH = 1u << 20;
     for (size_t o = 0; o < tasks.size(); o += CH) {
       size_t cnt = std::min(CH, tasks.size() - o);
       std::vector<GemmTask> sub(tasks.begin() + o, tasks.begin() + o + cnt);
       GemmTask* dt = sc.up(sub);
-      GemmTerm* dm = sc.up(terms);
-      launch_gemm(p, trA, trB, dt, dm, (int)cnt, maxM, maxN, sc.s);
+      if (o == 0) prof_note(flops, bytes * esz(p));
+      launch_gemm(p, dt, dm, (int)cnt, maxM, maxN, sc.s);
     }
   }
 };
@@ -192,6 +199,7 @@ struct Handle {
   std::vector<BoxRef> leaf_ref;
   std::vector<size_t> leaf_blk_off;          // element offset per near pair
   std::vector<size_t> leaf_pair_ptr;         // CSR row pointer over leaves
+  std::vector<size_t> leaf_mirror;           // pair index holding the stored block (i <= j)
   DBuf leaf_blk;
   std::vector<int> leaf_n;
   std::vector<int64_t> leaf_s;               // global tree-order start per leaf
@@ -285,6 +293,21 @@ static void build_heights(Handle& h) {
   }
 }
 
+// Leaf near block of pair (g, q): only pairs with g <= j are stored (the
+// kernels are symmetric, A_JI = A_IJ^T); the others reference the mirror.
+struct BlkRef {
+  const double* ptr;
+  int ld;
+  int tr;
+};
+static BlkRef leaf_block(const Handle& h, int g, size_t q) {
+  size_t pi = h.leaf_pair_ptr[g] + q;
+  int j = h.leaf_near[g][q];
+  if (g <= j) return BlkRef{h.leaf_blk.as<double>() + h.leaf_blk_off[pi], h.leaf_n[g], 0};
+  size_t mi = h.leaf_mirror[pi];
+  return BlkRef{h.leaf_blk.as<double>() + h.leaf_blk_off[mi], h.leaf_n[j], 1};
+}
+
 // The H^2 operator: per height, nested interpolative bases from the sampled
 // far-field block rows (eq. u with the low-rank blocks only), the far
 // skeleton blocks K(sk_I, sk_J) and the dense leaf near blocks.
@@ -295,17 +318,25 @@ static void build_operator(Handle& h) {
   int nleaf = (int)h.leaf_ref.size();
   h.leaf_pair_ptr.assign(nleaf + 1, 0);
   for (int g = 0; g < nleaf; ++g) h.leaf_pair_ptr[g + 1] = h.leaf_pair_ptr[g] + h.leaf_near[g].size();
-  h.leaf_blk_off.resize(h.leaf_pair_ptr[nleaf] + 1);
+  h.leaf_blk_off.assign(h.leaf_pair_ptr[nleaf] + 1, 0);
+  h.leaf_mirror.assign(h.leaf_pair_ptr[nleaf], 0);
   size_t tot = 0;
   for (int g = 0; g < nleaf; ++g)
     for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
-      h.leaf_blk_off[h.leaf_pair_ptr[g] + q] = tot;
-      tot += (size_t)h.leaf_n[g] * h.leaf_n[h.leaf_near[g][q]];
+      int j = h.leaf_near[g][q];
+      if (g <= j) {
+        h.leaf_blk_off[h.leaf_pair_ptr[g] + q] = tot;
+        tot += (size_t)h.leaf_n[g] * h.leaf_n[j];
+      } else {
+        const auto& nl = h.leaf_near[j];
+        size_t qq = std::find(nl.begin(), nl.end(), g) - nl.begin();
+        h.leaf_mirror[h.leaf_pair_ptr[g] + q] = h.leaf_pair_ptr[j] + qq;
+      }
     }
   h.leaf_blk_off[h.leaf_pair_ptr[nleaf]] = tot;
   if (h.opt.hbm_budget_bytes > 0 && (int64_t)(tot * 8) > h.opt.hbm_budget_bytes)
     throw StatusError(H2_ERR_BUDGET, "leaf near blocks alone need " + std::to_string(tot * 8) + " bytes");
-  h.leaf_blk.alloc(tot * 8);
+  h.leaf_blk.alloc(std::max<size_t>(1, tot) * 8);
   {
     Scratch sc(s);
     std::vector<AsmTask> tasks;
@@ -313,6 +344,7 @@ static void build_operator(Handle& h) {
     for (int g = 0; g < nleaf; ++g)
       for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
         int j = h.leaf_near[g][q];
+        if (g > j) continue;
         AsmTask a;
         a.out = h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[g] + q];
         a.ridx = nullptr;
@@ -473,8 +505,8 @@ static void matvec_tree(Handle& h, const double* x, double* y, int nrhs) {
       std::vector<GemmTerm> ts;
       for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
         int j = h.leaf_near[g][q];
-        ts.push_back(GemmTerm{h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[g] + q],
-                              x + h.leaf_s[j], h.leaf_n[j], h.leaf_n[g], (int)ld});
+        BlkRef br = leaf_block(h, (int)g, q);
+        ts.push_back(GemmTerm{br.ptr, x + h.leaf_s[j], h.leaf_n[j], br.ld, (int)ld, br.tr});
       }
       gb.add(y + h.leaf_s[g], (int)ld, h.leaf_n[g], nrhs, 1.0, 0.0, nullptr, 0, ts);
     }
@@ -644,8 +676,9 @@ static void root_factor(Handle& h, Root& rt, int spd) {
 
 // ------------------------------------------------------------- factor ----
 struct PairRef {
-  void* ptr;   // block pointer (work precision)
+  void* ptr;   // stored block (work precision)
   int ld;
+  int tr;      // 1: the pair's block is the transpose of the stored one
 };
 
 static void factor(Handle& h, int precision, int spd) {
@@ -684,7 +717,7 @@ static void factor(Handle& h, int precision, int spd) {
       for (auto& bx : pb.t.boxes[pb.t.L]) sizes.push_back((int)(bx.e - bx.s));
       setup_root(pb, sizes);
       // copy the leaf blocks into the root matrix
-      std::vector<CopyTask> ct;
+      std::vector<CopyTask> ct[2];
       int maxr = 0, maxc = 0;
       for (size_t g = 0; g < h.leaf_ref.size(); ++g) {
         if (h.leaf_ref[g].prob != (int)p) continue;
@@ -692,14 +725,16 @@ static void factor(Handle& h, int precision, int spd) {
         for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
           int jg = h.leaf_near[g][q];
           int j = h.leaf_ref[jg].local;
-          ct.push_back(CopyTask{h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[g] + q],
+          BlkRef br = leaf_block(h, (int)g, q);
+          ct[br.tr].push_back(CopyTask{br.ptr,
                                 (char*)pb.root.A->p + ((size_t)pb.root.off[i] + (size_t)pb.root.off[j] * pb.root.n) * ws,
-                                h.leaf_n[g], h.leaf_n[jg], h.leaf_n[g], pb.root.n});
+                                h.leaf_n[g], h.leaf_n[jg], br.ld, pb.root.n});
           maxr = std::max(maxr, h.leaf_n[g]);
           maxc = std::max(maxc, h.leaf_n[jg]);
         }
       }
-      launch_copy(Prec::F64, W, false, sc.up(ct), (int)ct.size(), maxr, maxc, s);
+      launch_copy(Prec::F64, W, false, sc.up(ct[0]), (int)ct[0].size(), maxr, maxc, s);
+      launch_copy(Prec::F64, W, true, sc.up(ct[1]), (int)ct[1].size(), maxr, maxc, s);
     }
     H2_CUDA(cudaStreamSynchronize(s));
   }
@@ -716,37 +751,38 @@ static void factor(Handle& h, int precision, int spd) {
     if (W == Prec::F64) {
       for (int g = 0; g < h0.nb; ++g) {
         int lg = leaf_of[g];
-        for (size_t q = 0; q < h0.near[g].size(); ++q)
-          Ablk[g].push_back(PairRef{h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[lg] + q], h.leaf_n[lg]});
+        for (size_t q = 0; q < h0.near[g].size(); ++q) {
+          BlkRef br = leaf_block(h, lg, q);
+          Ablk[g].push_back(PairRef{(void*)br.ptr, br.ld, br.tr});
+        }
       }
     } else {
-      // FP32 copy of the leaf near blocks for the mixed-precision pass
-      size_t tot = 0;
-      for (int g = 0; g < h0.nb; ++g) {
-        int lg = leaf_of[g];
-        tot += h.leaf_blk_off[h.leaf_pair_ptr[lg + 1]] - h.leaf_blk_off[h.leaf_pair_ptr[lg]];
-      }
-      auto buf = std::make_shared<DBuf>(tot * 4);
+      // FP32 copy of the stored (i <= j) leaf near blocks for the mixed pass
+      size_t tot = h.leaf_blk_off[h.leaf_pair_ptr[h.leaf_ref.size()]];
+      auto buf = std::make_shared<DBuf>(std::max<size_t>(1, tot) * 4);
       Aown.push_back(buf);
       Scratch sc(s);
       std::vector<CopyTask> ct;
-      size_t o = 0;
       int maxr = 0, maxc = 0;
-      for (int g = 0; g < h0.nb; ++g) {
-        int lg = leaf_of[g];
-        for (size_t q = 0; q < h0.near[g].size(); ++q) {
-          int jg = leaf_of[h0.near[g][q]];
-          size_t cnt = (size_t)h.leaf_n[lg] * h.leaf_n[jg];
-          float* dst = buf->as<float>() + o;
-          ct.push_back(CopyTask{h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[lg] + q], dst, h.leaf_n[lg],
-                                h.leaf_n[jg], h.leaf_n[lg], h.leaf_n[lg]});
-          Ablk[g].push_back(PairRef{dst, h.leaf_n[lg]});
-          o += cnt;
+      for (size_t lg = 0; lg < h.leaf_ref.size(); ++lg)
+        for (size_t q = 0; q < h.leaf_near[lg].size(); ++q) {
+          int jg = h.leaf_near[lg][q];
+          if ((int)lg > jg) continue;
+          size_t o = h.leaf_blk_off[h.leaf_pair_ptr[lg] + q];
+          ct.push_back(CopyTask{h.leaf_blk.as<double>() + o, buf->as<float>() + o, h.leaf_n[lg], h.leaf_n[jg],
+                                h.leaf_n[lg], h.leaf_n[lg]});
           maxr = std::max(maxr, h.leaf_n[lg]);
           maxc = std::max(maxc, h.leaf_n[jg]);
         }
-      }
       launch_copy(Prec::F64, Prec::F32, false, sc.up(ct), (int)ct.size(), maxr, maxc, s);
+      for (int g = 0; g < h0.nb; ++g) {
+        int lg = leaf_of[g];
+        for (size_t q = 0; q < h0.near[g].size(); ++q) {
+          BlkRef br = leaf_block(h, lg, q);
+          size_t o = (size_t)(br.ptr - h.leaf_blk.as<double>());
+          Ablk[g].push_back(PairRef{buf->as<float>() + o, br.ld, br.tr});
+        }
+      }
       H2_CUDA(cudaStreamSynchronize(s));
     }
     h0.n.resize(h0.nb);
@@ -802,7 +838,8 @@ static void factor(Handle& h, int precision, int spd) {
         for (size_t q = 0; q < ht.near[g].size(); ++q) {
           int j = ht.near[g][q];
           if (j == g) continue;
-          ts.push_back(GemmTerm{Ablk[g][q].ptr, Ablk[g][q].ptr, n[j], Ablk[g][q].ld, Ablk[g][q].ld});
+          int t = Ablk[g][q].tr;
+          ts.push_back(GemmTerm{Ablk[g][q].ptr, Ablk[g][q].ptr, n[j], Ablk[g][q].ld, Ablk[g][q].ld, t ? 3 : 0});
         }
         ng.add((char*)Mk + so[g] * ws, n[g], n[g], n[g], 1.0, 0.0, nullptr, 0, ts);
       }
@@ -850,8 +887,11 @@ static void factor(Handle& h, int precision, int spd) {
           int K = ht.near[g][k];
           if (K == g || !has_lu[K]) continue;
           void* V = (char*)Tmp + so[g] * ws;
-          g1.add1(V, n[g], n[g], n[K], Ablk[g][k].ptr, Ablk[g][k].ld, (char*)Mk + so[K] * ws, n[K], n[K]);
-          g2.add1((char*)GF + so[g] * ws, n[g], n[g], n[g], V, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K], 1.0, 1.0);
+          int t = Ablk[g][k].tr;
+          g1.add1(V, n[g], n[g], n[K], Ablk[g][k].ptr, Ablk[g][k].ld, (char*)Mk + so[K] * ws, n[K], n[K], 1.0, 0.0,
+                  nullptr, 0, t ? 1 : 0);
+          g2.add1((char*)GF + so[g] * ws, n[g], n[g], n[g], V, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K], 1.0, 1.0,
+                  nullptr, 0, t ? 2 : 0);
         }
         g1.run(W, false, false, sc);
         g2.run(W, false, true, sc);
@@ -1006,18 +1046,29 @@ static void factor(Handle& h, int precision, int spd) {
         up->n[pg] += r[g];
         up->cand[pg].insert(up->cand[pg].end(), ht.sk[g].begin(), ht.sk[g].end());
       }
+      // only pairs P <= Q are stored; (Q, P) references the transpose
       size_t tot = 0;
       std::vector<std::vector<size_t>> po(up->nb);
       for (int pg = 0; pg < up->nb; ++pg)
         for (int qg : up->near[pg]) {
           po[pg].push_back(tot);
-          tot += (size_t)up->n[pg] * up->n[qg];
+          if (pg <= qg) tot += (size_t)up->n[pg] * up->n[qg];
         }
+      if (h.opt.hbm_budget_bytes > 0 && (int64_t)(tot * ws) > h.opt.hbm_budget_bytes)
+        throw StatusError(H2_ERR_BUDGET, "level near blocks need " + std::to_string(tot * ws) + " bytes");
       Anext_buf = std::make_shared<DBuf>(std::max<size_t>(1, tot) * ws);
       Anext.assign(up->nb, {});
       for (int pg = 0; pg < up->nb; ++pg)
-        for (size_t q = 0; q < up->near[pg].size(); ++q)
-          Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[pg][q] * ws, up->n[pg]});
+        for (size_t q = 0; q < up->near[pg].size(); ++q) {
+          int qg = up->near[pg][q];
+          if (pg <= qg) {
+            Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[pg][q] * ws, up->n[pg], 0});
+          } else {
+            const auto& nl = up->near[qg];
+            size_t qq = std::find(nl.begin(), nl.end(), pg) - nl.begin();
+            Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[qg][qq] * ws, up->n[qg], 1});
+          }
+        }
     }
     // root setup for problems whose top ULV height is H
     for (size_t p = 0; p < h.probs.size(); ++p) {
@@ -1036,6 +1087,7 @@ static void factor(Handle& h, int precision, int spd) {
       int coloff = (ht.ref[j].local % 2) ? r[j - 1] : 0;
       if (pg >= 0) {
         int pj = ht.parent[j];
+        if (pg > pj) return nullptr;
         const auto& nl = up->near[pg];
         int q = (int)(std::find(nl.begin(), nl.end(), pj) - nl.begin());
         ld = Anext[pg][q].ld;
@@ -1068,10 +1120,12 @@ static void factor(Handle& h, int precision, int spd) {
           if (k >= ht.near[g].size()) continue;
           int j = ht.near[g][k];
           if (j == g) continue;
-          char* V = (char*)Tmp + so[g] * ws;   // n_g x r_j
-          g1.add1(V, n[g], n[g], r[j], Ablk[g][k].ptr, Ablk[g][k].ld, USp(j), n[j], n[j]);
           int ld;
           char* D = dest(g, j, ld);
+          if (!D) continue;                    // mirror of a stored parent block
+          char* V = (char*)Tmp + so[g] * ws;   // n_g x r_j
+          g1.add1(V, n[g], n[g], r[j], Ablk[g][k].ptr, Ablk[g][k].ld, USp(j), n[j], n[j], 1.0, 0.0, nullptr, 0,
+                  Ablk[g][k].tr ? 1 : 0);
           g2.add1(D, ld, r[g], r[j], USp(g), n[g], V, n[g], n[g]);
         }
         g1.run(W, false, false, sc);
@@ -1094,6 +1148,8 @@ static void factor(Handle& h, int precision, int spd) {
         for (int g = 0; g < nb; ++g) {
           if (k >= ht.far[g].size()) continue;
           int j = ht.far[g][k];
+          int ldd;
+          if (!dest(g, j, ldd)) continue;
           char* Kb = (char*)Tmp + so[g] * ws;           // r_g x r_j
           char* V = (char*)Mk + so[g] * ws;             // r_g x r_j
           at.push_back(AsmTask{Kb, dsk + sko[g], dsk + sko[j], 0, 0, r[g], r[j], r[g]});
@@ -1692,11 +1748,27 @@ h2_status h2_stats(h2_handle H, char* json, size_t cap) {
     }
     o << "],\"roots\":[";
     for (size_t p = 0; p < h.probs.size(); ++p) o << (p ? "," : "") << h.probs[p].root.n;
-    o << "]}";
+    o << "],\"launches\":" << prof().total_launches << ",\"kernels\":{";
+    prof().resolve();
+    bool first = true;
+    for (auto& kv : prof().stats) {
+      o << (first ? "" : ",") << "\"" << kv.first << "\":{\"launches\":" << kv.second.launches
+        << ",\"ms\":" << kv.second.ms << ",\"flops\":" << kv.second.flops << ",\"bytes\":" << kv.second.bytes
+        << "}";
+      first = false;
+    }
+    o << "}}";
     std::string sj = o.str();
     size_t n = std::min(cap - 1, sj.size());
     std::memcpy(json, sj.data(), n);
     json[n] = 0;
+  });
+}
+
+h2_status h2_profile(int32_t enable, int32_t reset) {
+  return guard([&] {
+    if (reset) prof().reset();
+    prof().timing = enable != 0;
   });
 }
 

@@ -87,6 +87,7 @@ struct GemmTerm {
   const void* A;
   const void* B;
   int K, lda, ldb;
+  int flags;          // bit 0: op(A) = A^T, bit 1: op(B) = B^T
 };
 struct GemmTask {
   void* C;            // output
@@ -179,7 +180,8 @@ struct InterpTask {    // P (n x r) from piv, T = R11^-1 R12 (r x (n-r), ld ldt)
 // ---------------------------------------------------------------------------
 enum class Prec { F64 = 0, F32 = 1 };
 
-void launch_gemm(Prec p, bool trA, bool trB, const GemmTask* d_tasks, const GemmTerm* d_terms,
+// Terms carry their own transposition flags (GemmTerm::flags).
+void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
                  int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64 = false);
 void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s);
 void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks,

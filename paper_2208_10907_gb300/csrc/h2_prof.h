@@ -1,0 +1,44 @@
+// Per-kernel launch counting and optional CUDA-event timing.  The caller of
+// a launch wrapper may note the algorithmic flops and bytes of the next
+// launch; with timing enabled each launch is bracketed by events on its own
+// stream and the durations are resolved when statistics are read.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+namespace h2 {
+
+struct KStat {
+  long long launches = 0;
+  double ms = 0.0, flops = 0.0, bytes = 0.0;
+};
+
+struct Prof {
+  bool timing = false;
+  std::map<std::string, KStat> stats;
+  struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  double next_flops = 0.0, next_bytes = 0.0;
+  long long total_launches = 0;
+  void resolve();
+  void reset();
+};
+
+Prof& prof();
+void prof_note(double flops, double bytes);
+
+struct ProfScope {
+  const char* name;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(const char* n, cudaStream_t st);
+  ~ProfScope();
+};
+
+}  // namespace h2

@@ -7,6 +7,7 @@
 // [U^R U^S]), the streamed fold of a far-field block row and the
 // interpolation matrix of the ID.
 #include "h2_common.cuh"
+#include "h2_prof.h"
 
 namespace h2 {
 
@@ -746,6 +747,7 @@ __global__ void logdet_kernel(const LuTask* __restrict__ tasks, double* out_log,
 // ------------------------------------------------------------ launchers ----
 void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s) {
   if (ntasks <= 0) return;
+  ProfScope ps(p == Prec::F64 ? "getrf_f64" : "getrf_f32", s);
   // panel rows up to a few thousand (root panels): smem = (m + nc) * sizeof(T)
   // is sized by the caller's maximum via the attribute below.
   size_t smem = (size_t)(8192 + 256) * (p == Prec::F64 ? 8 : 4);
@@ -783,6 +785,7 @@ static void trsm_dispatch(bool lower, bool unit, bool transA, const TrsmTask* d,
 void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks, int maxnrhs,
                  cudaStream_t s) {
   if (ntasks <= 0 || maxnrhs <= 0) return;
+  ProfScope ps(p == Prec::F64 ? "trsm_f64" : "trsm_f32", s);
   dim3 grid(ntasks, (maxnrhs + TS_COLS - 1) / TS_COLS);
   size_t smem = (size_t)256 * (TS_COLS + 1) * (p == Prec::F64 ? 8 : 4);
   if (p == Prec::F64) trsm_dispatch<double>(lower, unit, transA, d, grid, smem, s);
@@ -792,18 +795,21 @@ void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, 
 
 void launch_pchol(const CholTask* d, int ntasks, cudaStream_t s) {
   if (ntasks <= 0) return;
+  ProfScope ps("pchol_f64", s);
   pchol_kernel<<<ntasks, NT, 0, s>>>(d);
   H2_LAUNCH_CHECK();
 }
 
 void launch_pqr(const PqrTask* d, int ntasks, cudaStream_t s) {
   if (ntasks <= 0) return;
+  ProfScope ps("pqr_f64", s);
   pqr_kernel<<<ntasks, NT, 0, s>>>(d);
   H2_LAUNCH_CHECK();
 }
 
 void launch_hqr(Prec p, const HqrTask* d, int ntasks, cudaStream_t s) {
   if (ntasks <= 0) return;
+  ProfScope ps(p == Prec::F64 ? "hqr_f64" : "hqr_f32", s);
   if (p == Prec::F64) hqr_kernel<double><<<ntasks, NT, 0, s>>>(d);
   else hqr_kernel<float><<<ntasks, NT, 0, s>>>(d);
   H2_LAUNCH_CHECK();
@@ -811,6 +817,7 @@ void launch_hqr(Prec p, const HqrTask* d, int ntasks, cudaStream_t s) {
 
 void launch_fold(const FoldTask* d, int ntasks, Points pts, KParams kp, cudaStream_t s) {
   if (ntasks <= 0) return;
+  ProfScope ps("fold_f64", s);
   size_t smem = (size_t)FC * 257 * sizeof(double);
   H2_CUDA(cudaFuncSetAttribute(fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   fold_kernel<<<ntasks, NT, smem, s>>>(d, pts, kp);
@@ -819,6 +826,7 @@ void launch_fold(const FoldTask* d, int ntasks, Points pts, KParams kp, cudaStre
 
 void launch_kgram(Prec p, const KgramTask* d, int ntasks, int maxn, Points pts, KParams kp, cudaStream_t s) {
   if (ntasks <= 0 || maxn <= 0) return;
+  ProfScope ps(p == Prec::F64 ? "kgram_f64" : "kgram_f32", s);
   int t = (maxn + 63) / 64;
   dim3 grid(ntasks, t * t);
   if (p == Prec::F64) kgram_kernel<double><<<grid, NT, 0, s>>>(d, pts, kp);
@@ -829,6 +837,7 @@ void launch_kgram(Prec p, const KgramTask* d, int ntasks, int maxn, Points pts, 
 void launch_assemble(Prec p, const AsmTask* d, int ntasks, int maxr, int maxc, Points pts, KParams kp,
                      cudaStream_t s) {
   if (ntasks <= 0 || maxc <= 0) return;
+  ProfScope ps(p == Prec::F64 ? "assemble_f64" : "assemble_f32", s);
   dim3 grid(ntasks, maxc);
   if (p == Prec::F64) assemble_kernel<double><<<grid, NT, 0, s>>>(d, pts, kp);
   else assemble_kernel<float><<<grid, NT, 0, s>>>(d, pts, kp);
@@ -838,6 +847,7 @@ void launch_assemble(Prec p, const AsmTask* d, int ntasks, int maxr, int maxc, P
 void launch_copy(Prec src, Prec dst, bool transpose, const CopyTask* d, int ntasks, int maxr, int maxc,
                  cudaStream_t s) {
   if (ntasks <= 0) return;
+  ProfScope ps("copy", s);
   long long cnt = (long long)maxr * maxc;
   int gy = (int)std::min<long long>(64, (cnt + NT - 1) / NT);
   if (gy < 1) gy = 1;
@@ -855,6 +865,7 @@ void launch_copy(Prec src, Prec dst, bool transpose, const CopyTask* d, int ntas
 
 void launch_interp(Prec p, const InterpTask* d, int ntasks, cudaStream_t s) {
   if (ntasks <= 0) return;
+  ProfScope ps("interp", s);
   if (p == Prec::F64) interp_kernel<double><<<ntasks, NT, 0, s>>>(d);
   else interp_kernel<float><<<ntasks, NT, 0, s>>>(d);
   H2_LAUNCH_CHECK();
@@ -862,6 +873,7 @@ void launch_interp(Prec p, const InterpTask* d, int ntasks, cudaStream_t s) {
 
 void launch_colnorm2(const double* X, int n, int nrhs, int64_t ld, double* out, cudaStream_t s) {
   if (nrhs <= 0) return;
+  ProfScope ps("colnorm", s);
   colnorm2_kernel<<<nrhs, NT, 0, s>>>(X, n, nrhs, ld, out);
   H2_LAUNCH_CHECK();
 }
@@ -870,6 +882,7 @@ void launch_axpy_cols(double* Y, const double* X, int n, int nrhs, int64_t ldy, 
                       cudaStream_t s) {
   long long cnt = (long long)n * nrhs;
   if (cnt <= 0) return;
+  ProfScope ps("axpy", s);
   int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
   axpy_cols_kernel<<<g, NT, 0, s>>>(Y, X, n, nrhs, ldy, ldx, alpha);
   H2_LAUNCH_CHECK();
@@ -879,12 +892,14 @@ void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ld
                          int64_t n, int nrhs, bool scatter, cudaStream_t s) {
   long long cnt = (long long)n * nrhs;
   if (cnt <= 0) return;
+  ProfScope ps("permute", s);
   int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
   permute_rows_kernel<<<g, NT, 0, s>>>(src, lds, dst, ldd, map, n, nrhs, scatter);
   H2_LAUNCH_CHECK();
 }
 
 void launch_fill_eye(Prec p, void* A, int n, int ld, cudaStream_t s) {
+  ProfScope ps("eye", s);
   long long cnt = (long long)n * n;
   int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
   if (p == Prec::F64) eye_kernel<double><<<g, NT, 0, s>>>((double*)A, n, ld);
@@ -896,6 +911,7 @@ void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int 
                        cudaStream_t s) {
   (void)ncols;
   if (ce <= cb || k1 <= k0) return;
+  ProfScope ps("laswp", s);
   int g = std::min(152 * 4, (ce - cb + NT - 1) / NT);
   if (p == Prec::F64) laswp_kernel<double><<<g, NT, 0, s>>>((double*)A, lda, piv, k0, k1, cb, ce);
   else laswp_kernel<float><<<g, NT, 0, s>>>((float*)A, lda, piv, k0, k1, cb, ce);
@@ -905,6 +921,7 @@ void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int 
 void launch_logdet_lu(const LuTask* d, int ntasks, double* out_log, double* out_sign, bool cholesky,
                       cudaStream_t s) {
   if (ntasks <= 0) return;
+  ProfScope ps("logdet", s);
   logdet_kernel<<<ntasks, NT, 0, s>>>(d, out_log, out_sign, cholesky);
   H2_LAUNCH_CHECK();
 }

@@ -6,6 +6,7 @@
 // (eq. rs, eq. ss), the Schur updates, the near-field part of the H^2
 // matvec and the solve sweeps.
 #include "h2_common.cuh"
+#include "h2_prof.h"
 
 namespace h2 {
 
@@ -18,7 +19,7 @@ template <typename T> __device__ __forceinline__ T ld_elem(const void* p, long l
   return reinterpret_cast<const T*>(p)[idx];
 }
 
-template <typename T, bool TRA, bool TRB, bool F64IN>
+template <typename T, bool F64IN>
 __global__ void __launch_bounds__(NT) gemm_kernel(const GemmTask* __restrict__ tasks,
                                                   const GemmTerm* __restrict__ terms) {
   const GemmTask tk = tasks[blockIdx.x];
@@ -40,6 +41,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmTask* __restrict__ t
 
   for (int t = tk.t0; t < tk.t0 + tk.nt; ++t) {
     const GemmTerm tm = terms[t];
+    const bool TRA = (tm.flags & 1) != 0, TRB = (tm.flags & 2) != 0;   // uniform per CTA
     for (int k0 = 0; k0 < tm.K; k0 += BK) {
       // ---- stage op(A) tile (BM x BK) as As[k][i]
       if (!TRA) {
@@ -113,24 +115,21 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmTask* __restrict__ t
 }
 
 template <typename T, bool F64IN>
-void dispatch(bool trA, bool trB, const GemmTask* d_tasks, const GemmTerm* d_terms, int ntasks,
-              dim3 grid, cudaStream_t s) {
-  if (!trA && !trB) gemm_kernel<T, false, false, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
-  else if (!trA && trB) gemm_kernel<T, false, true, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
-  else if (trA && !trB) gemm_kernel<T, true, false, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
-  else gemm_kernel<T, true, true, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
+void dispatch(const GemmTask* d_tasks, const GemmTerm* d_terms, dim3 grid, cudaStream_t s) {
+  gemm_kernel<T, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
 }
 
 }  // namespace
 
-void launch_gemm(Prec p, bool trA, bool trB, const GemmTask* d_tasks, const GemmTerm* d_terms,
+void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
                  int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64) {
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return;
   int tiles = ((maxM + BM - 1) / BM) * ((maxN + BN - 1) / BN);
   dim3 grid(ntasks, tiles);
-  if (p == Prec::F64) dispatch<double, false>(trA, trB, d_tasks, d_terms, ntasks, grid, s);
-  else if (inputs_f64) dispatch<float, true>(trA, trB, d_tasks, d_terms, ntasks, grid, s);
-  else dispatch<float, false>(trA, trB, d_tasks, d_terms, ntasks, grid, s);
+  ProfScope ps(p == Prec::F64 ? "gemm_f64" : "gemm_f32", s);
+  if (p == Prec::F64) dispatch<double, false>(d_tasks, d_terms, grid, s);
+  else if (inputs_f64) dispatch<float, true>(d_tasks, d_terms, grid, s);
+  else dispatch<float, false>(d_tasks, d_terms, grid, s);
   H2_LAUNCH_CHECK();
 }
 

@@ -21,7 +21,7 @@ H2_FP64, H2_MIXED = 0, 1
 KERNEL_KIND = {"laplace": H2_K_LAPLACE, "yukawa": H2_K_YUKAWA, "matern32": H2_K_MATERN32}
 
 EXPORTED = ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_matvec",
-            "h2_logdet", "h2_stats", "h2_last_error", "h2_destroy")
+            "h2_logdet", "h2_stats", "h2_profile", "h2_last_error", "h2_destroy")
 
 
 class h2_kernel(ctypes.Structure):
@@ -61,10 +61,11 @@ def lib():
         L.h2_matvec.argtypes = [vp, vp, vp, i32, i64]
         L.h2_logdet.argtypes = [vp, vp, vp]
         L.h2_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+        L.h2_profile.argtypes = [i32, i32]
         L.h2_last_error.restype = ctypes.c_char_p
         L.h2_destroy.argtypes = [vp]
         for f in ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_matvec", "h2_logdet",
-                  "h2_stats"):
+                  "h2_stats", "h2_profile"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -142,6 +143,10 @@ def h2_stats(h, cap=1 << 16):
     buf = ctypes.create_string_buffer(cap)
     _check(lib().h2_stats(h, buf, cap))
     return buf.value.decode()
+
+
+def h2_profile(enable, reset=0):
+    _check(lib().h2_profile(int(enable), int(reset)))
 
 
 def h2_destroy(h):
