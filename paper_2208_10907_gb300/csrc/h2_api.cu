@@ -25,6 +25,38 @@
 namespace h2 {
 
 // ------------------------------------------------------------------ memory --
+// Allocation registry for the host-side task validator (H2_CHECK=1): every
+// task's address range is checked against the live device allocations
+// before its launch is issued.
+static std::map<uintptr_t, size_t>& registry() {
+  static std::map<uintptr_t, size_t> r;
+  return r;
+}
+static bool g_check = [] {
+  const char* e = getenv("H2_CHECK");
+  return e && e[0] == '1';
+}();
+
+static void check_range(const void* p, size_t bytes, const char* what) {
+  if (!g_check || p == nullptr || bytes == 0) return;
+  uintptr_t a = (uintptr_t)p;
+  auto& r = registry();
+  auto it = r.upper_bound(a);
+  if (it == r.begin())
+    throw StatusError(H2_ERR_ARG, std::string("validator: ") + what + " pointer outside every allocation");
+  --it;
+  if (a + bytes > it->first + it->second)
+    throw StatusError(H2_ERR_ARG, std::string("validator: ") + what + " range exceeds its allocation by " +
+                                      std::to_string((long long)(a + bytes - (it->first + it->second))) +
+                                      " bytes (offset " + std::to_string((long long)(a - it->first)) + " of " +
+                                      std::to_string((long long)it->second) + ")");
+}
+// extent in elements of an r x c column-major block with leading dim ld
+static size_t ext(long long r, long long c, long long ld) {
+  if (r <= 0 || c <= 0) return 0;
+  return (size_t)((c - 1) * ld + r);
+}
+
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -40,9 +72,11 @@ struct DBuf {
         (void)cudaGetLastError();
         throw StatusError(H2_ERR_OOM, "device allocation of " + std::to_string(b) + " bytes failed");
       }
+      registry()[(uintptr_t)p] = b;
     }
   }
   void release() {
+    if (p) registry().erase((uintptr_t)p);
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
@@ -74,6 +108,89 @@ struct Scratch {
 };
 
 static size_t esz(Prec p) { return p == Prec::F64 ? 8 : 4; }
+
+static void validate(const std::vector<GemmTask>& tasks, const std::vector<GemmTerm>& terms, size_t es) {
+  if (!g_check) return;
+  for (const GemmTask& t : tasks) {
+    check_range(t.C, ext(t.M, t.N, t.ldc) * es, "gemm C");
+    if (t.Cin && t.beta != 0.0) check_range(t.Cin, ext(t.M, t.N, t.ldcin) * es, "gemm Cin");
+    if (t.ldc < t.M) throw StatusError(H2_ERR_ARG, "validator: gemm ldc < M");
+    for (int q = t.t0; q < t.t0 + t.nt; ++q) {
+      const GemmTerm& m = terms[q];
+      bool ta = m.flags & 1, tb = m.flags & 2;
+      check_range(m.A, (ta ? ext(m.K, t.M, m.lda) : ext(t.M, m.K, m.lda)) * es, "gemm A");
+      check_range(m.B, (tb ? ext(t.N, m.K, m.ldb) : ext(m.K, t.N, m.ldb)) * es, "gemm B");
+      if ((ta ? m.K : t.M) > m.lda || (tb ? t.N : m.K) > m.ldb)
+        throw StatusError(H2_ERR_ARG, "validator: gemm leading dimension too small");
+    }
+  }
+}
+static void validate(const std::vector<TrsmTask>& v, size_t es) {
+  if (!g_check) return;
+  for (const TrsmTask& t : v) {
+    if (t.n > 256) throw StatusError(H2_ERR_ARG, "validator: trsm n > 256");
+    check_range(t.A, ext(t.n, t.n, t.lda) * es, "trsm A");
+    check_range(t.B, ext(t.n, t.nrhs, t.ldb) * es, "trsm B");
+    if (t.piv) check_range(t.piv, (size_t)t.n * 4, "trsm piv");
+  }
+}
+static void validate(const std::vector<LuTask>& v, size_t es) {
+  if (!g_check) return;
+  for (const LuTask& t : v) {
+    check_range(t.A, ext(t.m, t.nc, t.lda) * es, "getrf A");
+    check_range(t.piv, (size_t)t.nc * 4, "getrf piv");
+  }
+}
+static void validate(const std::vector<CopyTask>& v, size_t es_s, size_t es_d, bool tr) {
+  if (!g_check) return;
+  for (const CopyTask& t : v) {
+    check_range(t.src, (tr ? ext(t.cols, t.rows, t.lds) : ext(t.rows, t.cols, t.lds)) * es_s, "copy src");
+    check_range(t.dst, ext(t.rows, t.cols, t.ldd) * es_d, "copy dst");
+  }
+}
+static void validate(const std::vector<CholTask>& v) {
+  if (!g_check) return;
+  for (const CholTask& t : v) {
+    if (t.n > 256) throw StatusError(H2_ERR_ARG, "validator: pchol n > 256");
+    check_range(t.G, ext(t.n, t.n, t.ldg) * 8, "pchol G");
+    check_range(t.R, (size_t)t.n * t.n * 8, "pchol R");
+    check_range(t.piv, (size_t)t.n * 4, "pchol piv");
+    check_range(t.rank, 4, "pchol rank");
+  }
+}
+static void validate(const std::vector<KgramTask>& v) {
+  if (!g_check) return;
+  for (const KgramTask& t : v) {
+    check_range(t.G, ext(t.n, t.n, t.ldg) * 8, "kgram G");
+    check_range(t.cand, (size_t)t.n * 4, "kgram cand");
+    check_range(t.samp, (size_t)t.m * 4, "kgram samp");
+  }
+}
+static void validate(const std::vector<AsmTask>& v, size_t es) {
+  if (!g_check) return;
+  for (const AsmTask& t : v) {
+    check_range(t.out, ext(t.nr, t.nc, t.ld) * es, "assemble out");
+    if (t.ridx) check_range(t.ridx, (size_t)t.nr * 4, "assemble ridx");
+    if (t.cidx) check_range(t.cidx, (size_t)t.nc * 4, "assemble cidx");
+  }
+}
+static void validate(const std::vector<HqrTask>& v, size_t es) {
+  if (!g_check) return;
+  for (const HqrTask& t : v) {
+    check_range(t.M, (size_t)t.n * t.r * es, "hqr M");
+    check_range(t.V, (size_t)t.n * t.r * es, "hqr V");
+    check_range(t.Q, (size_t)t.n * t.n * es, "hqr Q");
+    check_range(t.W, (size_t)t.r * t.r * es, "hqr W");
+  }
+}
+static void validate(const std::vector<InterpTask>& v, size_t es) {
+  if (!g_check) return;
+  for (const InterpTask& t : v) {
+    check_range(t.P, (size_t)t.n * t.r * es, "interp P");
+    check_range(t.piv, (size_t)t.n * 4, "interp piv");
+    if (t.r < t.n) check_range(t.T, ext(t.r, t.n - t.r, t.ldt) * es, "interp T");
+  }
+}
 
 // ---------------------------------------------------------- GEMM batches --
 struct GemmBatch {
@@ -117,6 +234,7 @@ struct GemmBatch {
     if (tasks.empty()) return;
     const int fl = (trA ? 1 : 0) | (trB ? 2 : 0);
     for (GemmTerm& t : terms) t.flags ^= fl;
+    validate(tasks, terms, esz(p));
     GemmTerm* dm = sc.up(terms);
     const size_t CH = 1u << 20;
     for (size_t o = 0; o < tasks.size(); o += CH) {
@@ -128,6 +246,49 @@ struct GemmBatch {
     }
   }
 };
+
+
+// Validate (H2_CHECK=1), upload and launch.
+static void run_trsm(Prec p, bool lower, bool unit, bool tr, const std::vector<TrsmTask>& v, int maxrhs, Scratch& sc) {
+  if (v.empty()) return;
+  validate(v, esz(p));
+  launch_trsm(p, lower, unit, tr, sc.up(v), (int)v.size(), maxrhs, sc.s);
+}
+static void run_getrf(Prec p, const std::vector<LuTask>& v, Scratch& sc) {
+  if (v.empty()) return;
+  validate(v, esz(p));
+  launch_getrf(p, sc.up(v), (int)v.size(), sc.s);
+}
+static void run_copy(Prec a, Prec b, bool tr, const std::vector<CopyTask>& v, int mr, int mc, Scratch& sc) {
+  if (v.empty()) return;
+  validate(v, esz(a), esz(b), tr);
+  launch_copy(a, b, tr, sc.up(v), (int)v.size(), mr, mc, sc.s);
+}
+static void run_pchol(const std::vector<CholTask>& v, Scratch& sc) {
+  if (v.empty()) return;
+  validate(v);
+  launch_pchol(sc.up(v), (int)v.size(), sc.s);
+}
+static void run_kgram(Prec p, const std::vector<KgramTask>& v, int maxn, Points pts, KParams kp, Scratch& sc) {
+  if (v.empty()) return;
+  validate(v);
+  launch_kgram(p, sc.up(v), (int)v.size(), maxn, pts, kp, sc.s);
+}
+static void run_assemble(Prec p, const std::vector<AsmTask>& v, int mr, int mc, Points pts, KParams kp, Scratch& sc) {
+  if (v.empty()) return;
+  validate(v, esz(p));
+  launch_assemble(p, sc.up(v), (int)v.size(), mr, mc, pts, kp, sc.s);
+}
+static void run_hqr(Prec p, const std::vector<HqrTask>& v, Scratch& sc) {
+  if (v.empty()) return;
+  validate(v, esz(p));
+  launch_hqr(p, sc.up(v), (int)v.size(), sc.s);
+}
+static void run_interp(Prec p, const std::vector<InterpTask>& v, Scratch& sc) {
+  if (v.empty()) return;
+  validate(v, esz(p));
+  launch_interp(p, sc.up(v), (int)v.size(), sc.s);
+}
 
 // ------------------------------------------------------- handle structure --
 struct BoxRef {
@@ -359,7 +520,7 @@ static void build_operator(Handle& h) {
       }
     for (size_t o = 0; o < tasks.size(); o += (1u << 20)) {
       std::vector<AsmTask> sub(tasks.begin() + o, tasks.begin() + std::min(tasks.size(), o + (1u << 20)));
-      launch_assemble(Prec::F64, sc.up(sub), (int)sub.size(), 256, maxc, pts, h.kp, s);
+      run_assemble(Prec::F64, sub, 256, maxc, pts, h.kp, sc);
     }
     H2_CUDA(cudaStreamSynchronize(s));
   }
@@ -449,8 +610,8 @@ static void build_operator(Handle& h) {
       }
       it.push_back(InterpTask{piv + cand_off[g], Rq + r_off[g] + (size_t)r * n, ht.P_op[g]->p, n, r, n});
     }
-    launch_trsm(Prec::F64, false, false, false, sc.up(tt), (int)tt.size(), maxrhs, s);
-    launch_interp(Prec::F64, sc.up(it), (int)it.size(), s);
+    run_trsm(Prec::F64, false, false, false, tt, maxrhs, sc);
+    run_interp(Prec::F64, it, sc);
     // far skeleton blocks K(sk_I, sk_J)
     ht.far_off.assign(ht.nb + 1, 0);
     for (int g = 0; g < ht.nb; ++g) ht.far_off[g + 1] = ht.far_off[g] + ht.far[g].size();
@@ -472,7 +633,7 @@ static void build_operator(Handle& h) {
         at.push_back(AsmTask{blk->p, d_sk + sk_off[g], d_sk + sk_off[j], 0, 0, ht.r_op[g], ht.r_op[j], ht.r_op[g]});
         maxc = std::max(maxc, ht.r_op[j]);
       }
-    launch_assemble(Prec::F64, sc.up(at), (int)at.size(), 256, maxc, pts, h.kp, s);
+    run_assemble(Prec::F64, at, 256, maxc, pts, h.kp, sc);
     // skeleton-vector offsets
     ht.xh_off.assign(ht.nb + 1, 0);
     for (int g = 0; g < ht.nb; ++g) ht.xh_off[g + 1] = ht.xh_off[g] + ht.r_op[g];
@@ -603,7 +764,7 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   for (int k = 0; k < n; k += NB) {
     int nb = std::min(NB, n - k);
     std::vector<LuTask> lt{LuTask{A + k + (size_t)k * n, n - k, nb, n, piv + k, info}};
-    launch_getrf(Prec::F64, sc.up(lt), 1, s);
+    run_getrf(Prec::F64, lt, sc);
     // pivots are panel-relative: convert to global rows and apply to the
     // columns left and right of the panel
     std::vector<CopyTask> none;
@@ -620,7 +781,7 @@ static void root_factor(Handle& h, Root& rt, int spd) {
       // U12 = L11^-1 A12
       std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, A + k + (size_t)(k + nb) * n, nb, n - k - nb, n, n,
                                         nullptr}};
-      launch_trsm(Prec::F64, true, true, false, sc.up(tt), 1, n - k - nb, s);
+      run_trsm(Prec::F64, true, true, false, tt, n - k - nb, sc);
       // A22 -= L21 U12
       GemmBatch gb;
       gb.add1(A + (k + nb) + (size_t)(k + nb) * n, n, n - k - nb, n - k - nb, A + (k + nb) + (size_t)k * n, n,
@@ -653,7 +814,7 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   for (int k = 0; k < n; k += TB) {
     int nb = std::min(TB, n - k);
     std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, X + k, nb, n, n, n, nullptr}};
-    launch_trsm(Prec::F64, true, true, false, sc.up(tt), 1, n, s);
+    run_trsm(Prec::F64, true, true, false, tt, n, sc);
     if (k + nb < n) {
       GemmBatch gb;
       gb.add1(X + k + nb, n, n - k - nb, n, A + (k + nb) + (size_t)k * n, n, X + k, n, nb, -1.0, 1.0);
@@ -664,7 +825,7 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   for (int k = ((n - 1) / TB) * TB; k >= 0; k -= TB) {
     int nb = std::min(TB, n - k);
     std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, X + k, nb, n, n, n, nullptr}};
-    launch_trsm(Prec::F64, false, false, false, sc.up(tt), 1, n, s);
+    run_trsm(Prec::F64, false, false, false, tt, n, sc);
     if (k > 0) {
       GemmBatch gb;
       gb.add1(X, n, k, n, A + (size_t)k * n, n, X + k, n, nb, -1.0, 1.0);
@@ -733,8 +894,8 @@ static void factor(Handle& h, int precision, int spd) {
           maxc = std::max(maxc, h.leaf_n[jg]);
         }
       }
-      launch_copy(Prec::F64, W, false, sc.up(ct[0]), (int)ct[0].size(), maxr, maxc, s);
-      launch_copy(Prec::F64, W, true, sc.up(ct[1]), (int)ct[1].size(), maxr, maxc, s);
+      run_copy(Prec::F64, W, false, ct[0], maxr, maxc, sc);
+      run_copy(Prec::F64, W, true, ct[1], maxr, maxc, sc);
     }
     H2_CUDA(cudaStreamSynchronize(s));
   }
@@ -774,7 +935,7 @@ static void factor(Handle& h, int precision, int spd) {
           maxr = std::max(maxr, h.leaf_n[lg]);
           maxc = std::max(maxc, h.leaf_n[jg]);
         }
-      launch_copy(Prec::F64, Prec::F32, false, sc.up(ct), (int)ct.size(), maxr, maxc, s);
+      run_copy(Prec::F64, Prec::F32, false, ct, maxr, maxc, sc);
       for (int g = 0; g < h0.nb; ++g) {
         int lg = leaf_of[g];
         for (size_t q = 0; q < h0.near[g].size(); ++q) {
@@ -820,6 +981,7 @@ static void factor(Handle& h, int precision, int spd) {
     const size_t SL = (size_t)maxn * maxn;
     std::vector<size_t> so(nb + 1, 0);
     for (int g = 0; g <= nb; ++g) so[g] = (size_t)g * SL;
+    int* finfo = (int*)sc.alloc(4, true);
     void* LUK = sc.alloc(so[nb] * ws);
     int* pivK = (int*)sc.alloc((size_t)nb * 256 * 4);
     void* Mk = sc.alloc(so[nb] * ws, true);
@@ -833,7 +995,7 @@ static void factor(Handle& h, int precision, int spd) {
         int dq = diag_q(g);
         void* dst = (char*)LUK + so[g] * ws;
         ct.push_back(CopyTask{Ablk[g][dq].ptr, dst, n[g], n[g], Ablk[g][dq].ld, n[g]});
-        lu.push_back(LuTask{dst, n[g], n[g], n[g], pivK + (size_t)g * 256, nullptr});
+        lu.push_back(LuTask{dst, n[g], n[g], n[g], pivK + (size_t)g * 256, finfo});
         std::vector<GemmTerm> ts;
         for (size_t q = 0; q < ht.near[g].size(); ++q) {
           int j = ht.near[g][q];
@@ -843,8 +1005,8 @@ static void factor(Handle& h, int precision, int spd) {
         }
         ng.add((char*)Mk + so[g] * ws, n[g], n[g], n[g], 1.0, 0.0, nullptr, 0, ts);
       }
-      launch_copy(W, W, false, sc.up(ct), (int)ct.size(), maxn, maxn, s);
-      launch_getrf(W, sc.up(lu), (int)lu.size(), s);
+      run_copy(W, W, false, ct, maxn, maxn, sc);
+      run_getrf(W, lu, sc);
       ng.run(W, false, true, sc);
       // M_K = A_KK^-1 NG_K A_KK^-T  (NG symmetric): X = A^-1 NG; M = A^-1 X^T
       std::vector<TrsmTask> tl, tu;
@@ -857,11 +1019,9 @@ static void factor(Handle& h, int precision, int spd) {
         tu.push_back(TrsmTask{L, M, n[g], n[g], n[g], n[g], nullptr});
         tr.push_back(CopyTask{M, (char*)Tmp + so[g] * ws, n[g], n[g], n[g], n[g]});
       }
-      TrsmTask* dtl = sc.up(tl);
-      TrsmTask* dtu = sc.up(tu);
-      launch_trsm(W, true, true, false, dtl, (int)tl.size(), maxn, s);
-      launch_trsm(W, false, false, false, dtu, (int)tu.size(), maxn, s);
-      launch_copy(W, W, true, sc.up(tr), (int)tr.size(), maxn, maxn, s);
+      run_trsm(W, true, true, false, tl, maxn, sc);
+      run_trsm(W, false, false, false, tu, maxn, sc);
+      run_copy(W, W, true, tr, maxn, maxn, sc);
       std::vector<TrsmTask> tl2, tu2;
       for (int g = 0; g < nb; ++g) {
         if (!has_lu[g]) continue;
@@ -870,8 +1030,8 @@ static void factor(Handle& h, int precision, int spd) {
         tl2.push_back(TrsmTask{L, X, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
         tu2.push_back(TrsmTask{L, X, n[g], n[g], n[g], n[g], nullptr});
       }
-      launch_trsm(W, true, true, false, sc.up(tl2), (int)tl2.size(), maxn, s);
-      launch_trsm(W, false, false, false, sc.up(tu2), (int)tu2.size(), maxn, s);
+      run_trsm(W, true, true, false, tl2, maxn, sc);
+      run_trsm(W, false, false, false, tu2, maxn, sc);
       // M = Tmp (symmetric up to rounding)
       std::swap(Mk, Tmp);
     }
@@ -902,7 +1062,7 @@ static void factor(Handle& h, int precision, int spd) {
     {
       std::vector<CopyTask> ct;
       for (int g = 0; g < nb; ++g) ct.push_back(CopyTask{(char*)GF + so[g] * ws, G + off[g], n[g], n[g], n[g], n[g]});
-      launch_copy(W, Prec::F64, false, sc.up(ct), (int)ct.size(), maxn, maxn, s);
+      run_copy(W, Prec::F64, false, ct, maxn, maxn, sc);
       if (H > 0) {
         // point form: T^-1 G T^-T (T = blockdiag(W_a, W_b), upper triangular)
         double* G2 = (double*)sc.alloc(NN * 8);
@@ -913,9 +1073,9 @@ static void factor(Handle& h, int precision, int spd) {
           tr.push_back(CopyTask{G + off[g], G2 + off[g], n[g], n[g], n[g], n[g]});
           t2.push_back(TrsmTask{Tcur->as<double>() + t_off[g], G2 + off[g], n[g], n[g], n[g], n[g], nullptr});
         }
-        launch_trsm(Prec::F64, false, false, false, sc.up(t1), nb, maxn, s);
-        launch_copy(Prec::F64, Prec::F64, true, sc.up(tr), nb, maxn, maxn, s);
-        launch_trsm(Prec::F64, false, false, false, sc.up(t2), nb, maxn, s);
+        run_trsm(Prec::F64, false, false, false, t1, maxn, sc);
+        run_copy(Prec::F64, Prec::F64, true, tr, maxn, maxn, sc);
+        run_trsm(Prec::F64, false, false, false, t2, maxn, sc);
         G = G2;
       }
       // far-field block row Gram K(cand, samples) K(cand, samples)^T
@@ -938,22 +1098,35 @@ static void factor(Handle& h, int precision, int spd) {
         if (m == 0) continue;
         kt.push_back(KgramTask{dc + co[g], ds + sof[g], G + off[g], n[g], m, n[g], 1});
       }
-      launch_kgram(W, sc.up(kt), (int)kt.size(), maxn, pts, h.kp, s);
+      run_kgram(W, kt, maxn, pts, h.kp, sc);
     }
     double* R = (double*)sc.alloc(NN * 8);
     int* piv = (int*)sc.alloc((size_t)nb * 256 * 4);
     int* rank = (int*)sc.alloc((size_t)nb * 4);
+    int* cinfo = (int*)sc.alloc(8, true);   // [0] basis Gram non-finite, [1] fill-in LU zero pivot
+    H2_CUDA(cudaMemcpyAsync(cinfo + 1, finfo, 4, cudaMemcpyDeviceToDevice, s));
     {
+      // Rank tolerance of the fill-in basis.  In mixed precision the Gram
+      // matrix is accumulated in FP32, which resolves the block row only to
+      // about 2^-10 of its norm; pivoting below that would select skeletons
+      // from rounding noise (and grow the interpolation coefficients level by
+      // level), so the threshold is floored there.  The FP64 refinement
+      // against the H^2 operator recovers the accuracy.
+      const double tol_basis = (W == Prec::F32) ? std::max(h.opt.tol, 1.0 / 1024.0) : h.opt.tol;
       std::vector<CholTask> ct;
       for (int g = 0; g < nb; ++g)
-        ct.push_back(CholTask{G + off[g], n[g], n[g], piv + (size_t)g * 256, R + off[g], rank + g, h.opt.tol,
-                              h.opt.max_rank});
-      launch_pchol(sc.up(ct), nb, s);
+        ct.push_back(CholTask{G + off[g], n[g], n[g], piv + (size_t)g * 256, R + off[g], rank + g, tol_basis,
+                              h.opt.max_rank, cinfo});
+      run_pchol(ct, sc);
     }
     std::vector<int> hr(nb), hpiv((size_t)nb * 256);
+    int hci[2] = {0, 0};
     H2_CUDA(cudaMemcpyAsync(hr.data(), rank, nb * 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaMemcpyAsync(hpiv.data(), piv, hpiv.size() * 4, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaMemcpyAsync(hci, cinfo, 8, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaStreamSynchronize(s));
+    if (hci[0]) throw StatusError(H2_ERR_NONFINITE, "non-finite value in a basis Gram matrix");
+    if (hci[1]) throw StatusError(H2_ERR_SINGULAR, "zero or non-finite pivot in a diagonal-block LU (fill-ins)");
     ht.r.resize(nb);
     ht.sk.resize(nb);
     std::vector<int> keep_all(nb, 0);
@@ -987,8 +1160,8 @@ static void factor(Handle& h, int precision, int spd) {
         }
         it.push_back(InterpTask{piv + (size_t)g * 256, R + off[g] + (size_t)r[g] * n[g], P + off[g], n[g], r[g], n[g]});
       }
-      launch_trsm(Prec::F64, false, false, false, sc.up(tt), (int)tt.size(), maxrhs, s);
-      launch_interp(Prec::F64, sc.up(it), (int)it.size(), s);
+      run_trsm(Prec::F64, false, false, false, tt, maxrhs, sc);
+      run_interp(Prec::F64, it, sc);
       for (int g = 0; g < nb; ++g)
         if (keep_all[g]) launch_fill_eye(Prec::F64, P + off[g], n[g], n[g], s);
     }
@@ -1012,7 +1185,7 @@ static void factor(Handle& h, int precision, int spd) {
       std::vector<HqrTask> qt;
       for (int g = 0; g < nb; ++g)
         qt.push_back(HqrTask{Mm + off[g], V + off[g], ht.Q->as<double>() + off[g], ht.W->as<double>() + ht.w_off[g], n[g], r[g]});
-      launch_hqr(Prec::F64, sc.up(qt), nb, s);
+      run_hqr(Prec::F64, qt, sc);
     }
     const void* Qw = ht.Q->p;
     const void* Ww = ht.W->p;
@@ -1024,8 +1197,8 @@ static void factor(Handle& h, int precision, int spd) {
         ct.push_back(CopyTask{ht.Q->as<double>() + off[g], ht.Qw->as<float>() + off[g], n[g], n[g], n[g], n[g]});
         cw.push_back(CopyTask{ht.W->as<double>() + ht.w_off[g], Wf->as<float>() + ht.w_off[g], r[g], r[g], r[g], r[g]});
       }
-      launch_copy(Prec::F64, Prec::F32, false, sc.up(ct), nb, maxn, maxn, s);
-      launch_copy(Prec::F64, Prec::F32, false, sc.up(cw), nb, 256, 256, s);
+      run_copy(Prec::F64, Prec::F32, false, ct, maxn, maxn, sc);
+      run_copy(Prec::F64, Prec::F32, false, cw, 256, 256, sc);
       sc.bufs.push_back(Wf);
       Qw = ht.Qw->p;
       Ww = Wf->p;
@@ -1159,7 +1332,7 @@ static void factor(Handle& h, int precision, int spd) {
           char* D = dest(g, j, ld);
           g2.add1(D, ld, r[g], r[j], V, r[g], Wp(j), r[j], r[j]);
         }
-        launch_assemble(W, sc.up(at), (int)at.size(), 256, maxc, pts, h.kp, s);
+        run_assemble(W, at, 256, maxc, pts, h.kp, sc);
         g1.run(W, false, false, sc);
         g2.run(W, false, true, sc);
       }
@@ -1170,7 +1343,7 @@ static void factor(Handle& h, int precision, int spd) {
       std::vector<CopyTask> ct;
       for (int g = 0; g < nb; ++g)
         ct.push_back(CopyTask{(char*)Sw + off[g] * ws, ht.S->as<double>() + off[g], n[g], n[g], n[g], n[g]});
-      launch_copy(W, Prec::F64, false, sc.up(ct), nb, maxn, maxn, s);
+      run_copy(W, Prec::F64, false, ct, maxn, maxn, sc);
     }
     ht.pv_off.assign(nb + 1, 0);
     ht.lt_off.assign(nb + 1, 0);
@@ -1199,10 +1372,10 @@ static void factor(Handle& h, int precision, int spd) {
         maxm = std::max(maxm, m[g]);
       }
       if (!lu.empty()) {
-        launch_getrf(Prec::F64, sc.up(lu), (int)lu.size(), s);
-        launch_trsm(Prec::F64, true, true, false, sc.up(trs), (int)trs.size(), maxr, s);
-        launch_copy(Prec::F64, Prec::F64, true, sc.up(tr), (int)tr.size(), maxm, maxr, s);
-        launch_trsm(Prec::F64, true, false, true, sc.up(tsr), (int)tsr.size(), maxr, s);
+        run_getrf(Prec::F64, lu, sc);
+        run_trsm(Prec::F64, true, true, false, trs, maxr, sc);
+        run_copy(Prec::F64, Prec::F64, true, tr, maxm, maxr, sc);
+        run_trsm(Prec::F64, true, false, true, tsr, maxr, sc);
         // Schur: S^SS -= (L^SR) U^RS = Lt^T U^RS
         GemmBatch gb;
         for (int g = 0; g < nb; ++g) {
@@ -1221,7 +1394,7 @@ static void factor(Handle& h, int precision, int spd) {
         char* D = dest(g, g, ld);
         cs.push_back(CopyTask{S + off[g] + m[g] + (size_t)m[g] * n[g], D, r[g], r[g], n[g], ld});
       }
-      launch_copy(Prec::F64, W, false, sc.up(cs), nb, 256, 256, s);
+      run_copy(Prec::F64, W, false, cs, 256, 256, sc);
     }
     int hinfo = 0;
     H2_CUDA(cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, s));
@@ -1241,7 +1414,7 @@ static void factor(Handle& h, int precision, int spd) {
         ct.push_back(CopyTask{ht.W->as<double>() + ht.w_off[g], Tn->as<double>() + to[pg] + o + (size_t)o * up->n[pg],
                               r[g], r[g], r[g], up->n[pg]});
       }
-      launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 256, 256, s);
+      run_copy(Prec::F64, Prec::F64, false, ct, 256, 256, sc);
       H2_CUDA(cudaStreamSynchronize(s));
       Tcur = Tn;
       t_off = to;
@@ -1262,7 +1435,7 @@ static void factor(Handle& h, int precision, int spd) {
     if (rt.n == 0) continue;
     Scratch sc(s);
     std::vector<CopyTask> ct{CopyTask{rt.A->p, rt.LU->p, rt.n, rt.n, rt.n, rt.n}};
-    launch_copy(W, Prec::F64, false, sc.up(ct), 1, rt.n, rt.n, s);
+    run_copy(W, Prec::F64, false, ct, rt.n, rt.n, sc);
     root_factor(h, rt, spd);
     rt.A.reset();
   }
@@ -1292,7 +1465,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
     for (size_t p = 0; p < h.probs.size(); ++p)
       if (h.probs[p].H == 0)
         ct.push_back(CopyTask{b + h.probs[p].off, rootb[p], h.probs[p].root.n, nrhs, (int)ld, h.probs[p].root.n});
-    launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 8192, nrhs, s);
+    run_copy(Prec::F64, Prec::F64, false, ct, 8192, nrhs, sc);
   }
   // forward sweep
   for (int H = 0; H < h.Hmax; ++H) {
@@ -1326,7 +1499,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
       g2.add1(c[H] + ht.v_off[g] + m, (int)lv, ht.r[g], nrhs, ht.Lt->as<double>() + ht.lt_off[g], m,
               c[H] + ht.v_off[g], (int)lv, m, -1.0, 1.0);
     }
-    launch_trsm(Prec::F64, true, true, false, sc.up(tl), (int)tl.size(), nrhs, s);
+    run_trsm(Prec::F64, true, true, false, tl, nrhs, sc);
     g2.run(Prec::F64, true, false, sc);
     // gather skeleton parts into the next height's input (stored in xo[H])
     std::vector<CopyTask> ct;
@@ -1346,7 +1519,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
     if (H + 1 < h.Hmax) {
       // xo[H] is sized by height H; the parent vector is shorter, fits
     }
-    launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 256, nrhs, s);
+    run_copy(Prec::F64, Prec::F64, false, ct, 256, nrhs, sc);
   }
   // root solves
   {
@@ -1363,7 +1536,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
     for (size_t p = 0; p < h.probs.size(); ++p)
       if (h.probs[p].H == 0)
         ct.push_back(CopyTask{rootx[p], x + h.probs[p].off, h.probs[p].root.n, nrhs, h.probs[p].root.n, (int)ld});
-    launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 8192, nrhs, s);
+    run_copy(Prec::F64, Prec::F64, false, ct, 8192, nrhs, sc);
   }
   // backward sweep
   for (int H = h.Hmax - 1; H >= 0; --H) {
@@ -1387,7 +1560,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
       }
       ct.push_back(CopyTask{src, c[H] + ht.v_off[g] + m, ht.r[g], nrhs, lds, (int)lv});
     }
-    launch_copy(Prec::F64, Prec::F64, false, sc.up(ct), (int)ct.size(), 256, nrhs, s);
+    run_copy(Prec::F64, Prec::F64, false, ct, 256, nrhs, sc);
     GemmBatch g1;
     std::vector<TrsmTask> tu;
     for (int g = 0; g < nb; ++g) {
@@ -1399,7 +1572,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
       tu.push_back(TrsmTask{Sg, c[H] + ht.v_off[g], m, nrhs, ht.n[g], (int)lv, nullptr});
     }
     g1.run(Prec::F64, false, false, sc);
-    launch_trsm(Prec::F64, false, false, false, sc.up(tu), (int)tu.size(), nrhs, s);
+    run_trsm(Prec::F64, false, false, false, tu, nrhs, sc);
     GemmBatch g2;
     for (int g = 0; g < nb; ++g) {
       double* dst;

@@ -119,6 +119,7 @@ struct CholTask {      // pivoted Cholesky of an n x n Gram matrix (in place)
   int* rank;
   double tol;
   int max_rank;
+  int* info;           // set to 1 if a non-finite value is met (may be null)
 };
 
 struct PqrTask {       // Householder QR with column pivoting of an m x n matrix

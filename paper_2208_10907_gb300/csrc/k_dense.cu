@@ -91,6 +91,10 @@ __global__ void __launch_bounds__(NT) getrf_kernel(const LuTask* __restrict__ ta
     T pv;
     int p;
     block_argmax(best, bi, s_val, s_idx, pv, p);
+    if (p < k || p >= m) {   // every candidate was NaN: keep the row, flag the panel
+      p = k;
+      if (threadIdx.x == 0 && tk.info) atomicCAS(tk.info, 0, k + 1);
+    }
     if (threadIdx.x == 0) tk.piv[k] = p;
     if (p != k) {
       for (int j = threadIdx.x; j < nc; j += NT) {
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(NT) getrf_kernel(const LuTask* __restrict__ ta
     }
     __syncthreads();
     T akk = A[k + (long long)k * lda];
-    if (akk == (T)0) {
+    if (akk == (T)0 || akk != akk) {
       if (!singular && threadIdx.x == 0 && tk.info) atomicCAS(tk.info, 0, k + 1);
       singular = true;
       __syncthreads();
@@ -228,6 +232,11 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
     double pv;
     int p;
     block_argmax(best, bi, s_val, s_idx, pv, p);
+    if (p < k || p >= n) {   // NaN on the remaining diagonal: stop here, flag it
+      if (threadIdx.x == 0 && tk.info) *tk.info = 1;
+      rank = k;
+      break;
+    }
     if (p != k) {
       // symmetric swap of rows/cols k and p of the trailing matrix (full matrix)
       for (int j = threadIdx.x; j < n; j += NT) {
@@ -254,6 +263,11 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
       __syncthreads();
     }
     double gkk = G[k + (long long)k * ld];
+    if (gkk != gkk || fabs(gkk) == INFINITY) {
+      if (threadIdx.x == 0 && tk.info) *tk.info = 1;
+      rank = k;
+      break;
+    }
     if (k == 0) d1 = gkk;
     if (k >= tk.max_rank || gkk <= tk.tol * tk.tol * d1 || gkk <= 0.0) {
       rank = k;
@@ -321,6 +335,10 @@ __global__ void __launch_bounds__(NT) pqr_kernel(const PqrTask* __restrict__ tas
     double pv;
     int p;
     block_argmax(best, bi, s_val, s_idx, pv, p);
+    if (p < k || p >= n) {   // NaN column norms: stop here
+      rank = k;
+      break;
+    }
     if (p != k) {
       for (int i = threadIdx.x; i < m; i += NT) {
         double a = A[i + (long long)k * lda];
