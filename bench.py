@@ -194,33 +194,25 @@ def main():
     H.h2_profile(1, 1)
     barrier()
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     evf = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev0.record(stream)
     iters = []
+    evs[0].record(stream)
     for k in range(args.steps):
         H.h2_factor(h, H.H2_MIXED)
         evf[k].record(stream)
         st, ach, it = H.h2_solve(h, b, x, 1, n, W["target"], 30)
+        evs[k + 1].record(stream)
         iters.append((int(st), float(ach[0]), int(it)))
-    ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    total_ms = ev0.elapsed_time(ev1)
+    total_ms = evs[0].elapsed_time(evs[-1])
     stats = json.loads(H.h2_stats(h))
     H.h2_profile(0, 0)
-    fac_ms = [(ev0 if k == 0 else None) for k in range(args.steps)]
-    # factor / solve split from the per-step events
-    starts = [ev0] + []
-    f_ms, s_ms = [], []
-    prev = ev0
-    # each step: prev -> evf[k] is the factor; evf[k] -> next start is the solve
-    for k in range(args.steps):
-        f_ms.append(prev.elapsed_time(evf[k]))
-        prev = evf[k]
+    f_ms = [evs[k].elapsed_time(evf[k]) for k in range(args.steps)]
+    s_ms = [evf[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     step_ms = total_ms / args.steps
-    solve_ms = step_ms - float(np.mean(f_ms)) if len(f_ms) > 1 else total_ms - f_ms[0]
+    solve_ms = float(np.mean(s_ms))
     # max over ranks
     t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
     if world > 1:

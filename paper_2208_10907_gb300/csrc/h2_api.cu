@@ -290,6 +290,126 @@ static void run_interp(Prec p, const std::vector<InterpTask>& v, Scratch& sc) {
   launch_interp(p, sc.up(v), (int)v.size(), sc.s);
 }
 
+
+// ------------------------------------------------------------------ plans --
+// A fixed sequence of batched launches with device-resident task arrays,
+// replayed without host work; captured once into a CUDA graph.
+struct Op {
+  int kind;             // 0 gemm, 1 trsm, 2 copy, 3 axpy-free marker
+  Prec p, p2;
+  bool f1, f2, f3;
+  const void* tasks;
+  const void* terms;
+  int n, a, b;
+};
+
+struct Plan {
+  std::vector<Op> ops;
+  std::vector<DBufP> bufs;   // task arrays and workspaces
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t s = nullptr;
+  template <class T> T* up(const std::vector<T>& v) {
+    if (v.empty()) return nullptr;
+    auto b = std::make_shared<DBuf>(v.size() * sizeof(T));
+    H2_CUDA(cudaMemcpy(b->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    bufs.push_back(b);
+    return b->template as<T>();
+  }
+  double* work(size_t elems, bool zero = false) {
+    auto b = std::make_shared<DBuf>(std::max<size_t>(elems, 2) * 8);
+    if (zero) H2_CUDA(cudaMemset(b->p, 0, b->bytes));
+    bufs.push_back(b);
+    return b->template as<double>();
+  }
+  void gemm(Prec p, GemmBatch& gb, bool trA, bool trB) {
+    if (gb.tasks.empty()) return;
+    const int fl = (trA ? 1 : 0) | (trB ? 2 : 0);
+    for (GemmTerm& t : gb.terms) t.flags ^= fl;
+    validate(gb.tasks, gb.terms, esz(p));
+    Op o{};
+    o.kind = 0;
+    o.p = p;
+    o.tasks = up(gb.tasks);
+    o.terms = up(gb.terms);
+    o.n = (int)gb.tasks.size();
+    o.a = gb.maxM;
+    o.b = gb.maxN;
+    ops.push_back(o);
+  }
+  void trsm(Prec p, bool lower, bool unit, bool tr, const std::vector<TrsmTask>& v, int maxrhs) {
+    if (v.empty()) return;
+    validate(v, esz(p));
+    Op o{};
+    o.kind = 1;
+    o.p = p;
+    o.f1 = lower;
+    o.f2 = unit;
+    o.f3 = tr;
+    o.tasks = up(v);
+    o.n = (int)v.size();
+    o.a = maxrhs;
+    ops.push_back(o);
+  }
+  void copy(Prec a, Prec b, bool tr, const std::vector<CopyTask>& v, int mr, int mc) {
+    if (v.empty()) return;
+    validate(v, esz(a), esz(b), tr);
+    Op o{};
+    o.kind = 2;
+    o.p = a;
+    o.p2 = b;
+    o.f1 = tr;
+    o.tasks = up(v);
+    o.n = (int)v.size();
+    o.a = mr;
+    o.b = mc;
+    ops.push_back(o);
+  }
+  void issue(cudaStream_t st) const {
+    for (const Op& o : ops) {
+      if (o.kind == 0) launch_gemm(o.p, (const GemmTask*)o.tasks, (const GemmTerm*)o.terms, o.n, o.a, o.b, st);
+      else if (o.kind == 1) launch_trsm(o.p, o.f1, o.f2, o.f3, (const TrsmTask*)o.tasks, o.n, o.a, st);
+      else if (o.kind == 2) launch_copy(o.p, o.p2, o.f1, (const CopyTask*)o.tasks, o.n, o.a, o.b, st);
+    }
+  }
+  // replay: through the captured graph when profiling is off, else launch by
+  // launch (so each kernel is timed on its own)
+  void run(cudaStream_t st) {
+    if (prof().timing || getenv("H2_NO_GRAPH")) {
+      issue(st);
+      return;
+    }
+    if (!exec || st != s) {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      exec = nullptr;
+      graph = nullptr;
+      s = st;
+      cudaStream_t cs = st;
+      bool own = false;
+      if (cs == nullptr) {   // the legacy default stream cannot be captured
+        H2_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        own = true;
+      }
+      H2_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      issue(cs);
+      H2_CUDA(cudaStreamEndCapture(cs, &graph));
+      H2_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      if (own) {
+        H2_CUDA(cudaStreamSynchronize(cs));
+        cudaStreamDestroy(cs);
+      }
+    }
+    H2_CUDA(cudaGraphLaunch(exec, st));
+    prof().total_launches += (long long)ops.size();
+  }
+  ~Plan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+using PlanP = std::shared_ptr<Plan>;
+
 // ------------------------------------------------------- handle structure --
 struct BoxRef {
   int prob, level, local;
@@ -366,6 +486,14 @@ struct Handle {
   std::vector<int64_t> leaf_s;               // global tree-order start per leaf
   bool factored = false;
   int precision = 0, spd = 0;
+  // solve-time plans, per right-hand-side count: workspaces and launch lists
+  struct SolvePlans {
+    int nrhs = 0;
+    double *B = nullptr, *X = nullptr, *R = nullptr, *Uin = nullptr, *Uout = nullptr, *nrm = nullptr;
+    PlanP ulv, mv;
+    std::vector<DBufP> bufs;
+  };
+  std::map<int, std::shared_ptr<SolvePlans>> plans;
   double t_construct_ms = 0, t_factor_ms = 0;
   std::vector<double> level_ms;
   std::string stats_extra;
@@ -654,10 +782,10 @@ static void build_operator(Handle& h) {
 }
 
 // ------------------------------------------------------------- matvec ----
-// y = A_H2 x in tree order (N x nrhs, column-major, ld = Ntot).
-static void matvec_tree(Handle& h, const double* x, double* y, int nrhs) {
-  cudaStream_t s = h.s;
-  Scratch sc(s);
+// Plan of y = A_H2 x in tree order (N x nrhs, column-major, ld = Ntot).
+static PlanP build_matvec_plan(Handle& h, const double* x, double* y, int nrhs) {
+  auto P = std::make_shared<Plan>();
+  Plan& pl = *P;
   const int64_t ld = h.Ntot;
   // near part (leaf dense blocks): y_I = sum_J A_IJ x_J
   {
@@ -671,14 +799,14 @@ static void matvec_tree(Handle& h, const double* x, double* y, int nrhs) {
       }
       gb.add(y + h.leaf_s[g], (int)ld, h.leaf_n[g], nrhs, 1.0, 0.0, nullptr, 0, ts);
     }
-    gb.run(Prec::F64, false, false, sc);
+    pl.gemm(Prec::F64, gb, false, false);
   }
-  if (h.Hmax == 0) return;
+  if (h.Hmax == 0) return P;
   // upward pass
   std::vector<double*> xh(h.Hmax), yh(h.Hmax);
   for (int H = 0; H < h.Hmax; ++H) {
-    xh[H] = (double*)sc.alloc((size_t)h.hs[H].xh_len * nrhs * 8);
-    yh[H] = (double*)sc.alloc((size_t)h.hs[H].xh_len * nrhs * 8, true);
+    xh[H] = pl.work((size_t)h.hs[H].xh_len * nrhs);
+    yh[H] = pl.work((size_t)h.hs[H].xh_len * nrhs, true);
   }
   for (int H = 0; H < h.Hmax; ++H) {
     Height& ht = h.hs[H];
@@ -701,9 +829,10 @@ static void matvec_tree(Handle& h, const double* x, double* y, int nrhs) {
       gb.add1(xh[H] + ht.xh_off[g], (int)ht.xh_len, ht.r_op[g], nrhs, ht.P_op[g]->p, ht.n_op[g], src, (int)lds,
               ht.n_op[g]);
     }
-    gb.run(Prec::F64, true, false, sc);
+    pl.gemm(Prec::F64, gb, true, false);
   }
-  // far interactions at every height
+  // far interactions at every height (every box gets a task, so the
+  // skeleton vectors are overwritten on each replay)
   for (int H = 0; H < h.Hmax; ++H) {
     Height& ht = h.hs[H];
     GemmBatch gb;
@@ -714,9 +843,9 @@ static void matvec_tree(Handle& h, const double* x, double* y, int nrhs) {
         ts.push_back(GemmTerm{ht.Kfar_op[ht.far_off[g] + q]->p, xh[H] + ht.xh_off[j], ht.r_op[j], ht.r_op[g],
                               (int)ht.xh_len});
       }
-      if (!ts.empty()) gb.add(yh[H] + ht.xh_off[g], (int)ht.xh_len, ht.r_op[g], nrhs, 1.0, 0.0, nullptr, 0, ts);
+      gb.add(yh[H] + ht.xh_off[g], (int)ht.xh_len, ht.r_op[g], nrhs, 1.0, 0.0, nullptr, 0, ts);
     }
-    gb.run(Prec::F64, false, false, sc);
+    pl.gemm(Prec::F64, gb, false, false);
   }
   // downward pass: yh(children) += P_P yh(P)
   for (int H = h.Hmax - 1; H >= 1; --H) {
@@ -729,7 +858,7 @@ static void matvec_tree(Handle& h, const double* x, double* y, int nrhs) {
       gb.add1(dst, (int)dn.xh_len, ht.n_op[g], nrhs, ht.P_op[g]->p, ht.n_op[g], yh[H] + ht.xh_off[g],
               (int)ht.xh_len, ht.r_op[g], 1.0, 1.0);
     }
-    gb.run(Prec::F64, false, false, sc);
+    pl.gemm(Prec::F64, gb, false, false);
   }
   // leaf: y_I += P_I yh(I)
   {
@@ -742,9 +871,9 @@ static void matvec_tree(Handle& h, const double* x, double* y, int nrhs) {
       gb.add1(dst, (int)ld, ht.n_op[g], nrhs, ht.P_op[g]->p, ht.n_op[g], yh[0] + ht.xh_off[g], (int)ht.xh_len,
               ht.r_op[g], 1.0, 1.0);
     }
-    gb.run(Prec::F64, false, false, sc);
+    pl.gemm(Prec::F64, gb, false, false);
   }
-  H2_CUDA(cudaStreamSynchronize(s));
+  return P;
 }
 
 // ------------------------------------------------------------ root LU ----
@@ -1443,21 +1572,22 @@ static void factor(Handle& h, int precision, int spd) {
 }
 
 // -------------------------------------------------------------- solve ----
-// x = ULV^-1 b in tree order (N x nrhs, ld = Ntot), FP64 sweeps.
-static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
-  cudaStream_t s = h.s;
-  Scratch sc(s);
+// Plan of x = ULV^-1 b in tree order (N x nrhs, ld = Ntot), FP64 sweeps:
+// forward (L z = U^T b), root solve, backward (U y = z, x = V^T y).
+static PlanP build_ulv_plan(Handle& h, const double* b, double* x, int nrhs) {
+  auto P = std::make_shared<Plan>();
+  Plan& pl = *P;
   const int64_t ld = h.Ntot;
   std::vector<double*> c(h.Hmax), xo(h.Hmax);
   for (int H = 0; H < h.Hmax; ++H) {
-    c[H] = (double*)sc.alloc((size_t)h.hs[H].v_len * nrhs * 8);
-    xo[H] = (double*)sc.alloc((size_t)h.hs[H].v_len * nrhs * 8);
+    c[H] = pl.work((size_t)h.hs[H].v_len * nrhs);
+    xo[H] = pl.work((size_t)h.hs[H].v_len * nrhs);
   }
   std::vector<double*> rootb(h.probs.size(), nullptr), rootx(h.probs.size(), nullptr);
   for (size_t p = 0; p < h.probs.size(); ++p)
     if (h.probs[p].root.n) {
-      rootb[p] = (double*)sc.alloc((size_t)h.probs[p].root.n * nrhs * 8);
-      rootx[p] = (double*)sc.alloc((size_t)h.probs[p].root.n * nrhs * 8);
+      rootb[p] = pl.work((size_t)h.probs[p].root.n * nrhs);
+      rootx[p] = pl.work((size_t)h.probs[p].root.n * nrhs);
     }
   // problems without ULV heights: root rhs = the whole problem
   {
@@ -1465,7 +1595,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
     for (size_t p = 0; p < h.probs.size(); ++p)
       if (h.probs[p].H == 0)
         ct.push_back(CopyTask{b + h.probs[p].off, rootb[p], h.probs[p].root.n, nrhs, (int)ld, h.probs[p].root.n});
-    run_copy(Prec::F64, Prec::F64, false, ct, 8192, nrhs, sc);
+    pl.copy(Prec::F64, Prec::F64, false, ct, 8192, nrhs);
   }
   // forward sweep
   for (int H = 0; H < h.Hmax; ++H) {
@@ -1488,7 +1618,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
       g1.add1(c[H] + ht.v_off[g], (int)lv, ht.n[g], nrhs, ht.Q->as<double>() + ht.q_off[g], ht.n[g], src, (int)lds,
               ht.n[g]);
     }
-    g1.run(Prec::F64, true, false, sc);
+    pl.gemm(Prec::F64, g1, true, false);
     std::vector<TrsmTask> tl;
     GemmBatch g2;
     for (int g = 0; g < nb; ++g) {
@@ -1499,8 +1629,8 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
       g2.add1(c[H] + ht.v_off[g] + m, (int)lv, ht.r[g], nrhs, ht.Lt->as<double>() + ht.lt_off[g], m,
               c[H] + ht.v_off[g], (int)lv, m, -1.0, 1.0);
     }
-    run_trsm(Prec::F64, true, true, false, tl, nrhs, sc);
-    g2.run(Prec::F64, true, false, sc);
+    pl.trsm(Prec::F64, true, true, false, tl, nrhs);
+    pl.gemm(Prec::F64, g2, true, false);
     // gather skeleton parts into the next height's input (stored in xo[H])
     std::vector<CopyTask> ct;
     for (int g = 0; g < nb; ++g) {
@@ -1519,7 +1649,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
     if (H + 1 < h.Hmax) {
       // xo[H] is sized by height H; the parent vector is shorter, fits
     }
-    run_copy(Prec::F64, Prec::F64, false, ct, 256, nrhs, sc);
+    pl.copy(Prec::F64, Prec::F64, false, ct, 256, nrhs);
   }
   // root solves
   {
@@ -1529,14 +1659,14 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
       if (!rt.n) continue;
       gb.add1(rootx[p], rt.n, rt.n, nrhs, rt.inv->p, rt.n, rootb[p], rt.n, rt.n);
     }
-    gb.run(Prec::F64, false, false, sc);
+    pl.gemm(Prec::F64, gb, false, false);
   }
   {
     std::vector<CopyTask> ct;
     for (size_t p = 0; p < h.probs.size(); ++p)
       if (h.probs[p].H == 0)
         ct.push_back(CopyTask{rootx[p], x + h.probs[p].off, h.probs[p].root.n, nrhs, h.probs[p].root.n, (int)ld});
-    run_copy(Prec::F64, Prec::F64, false, ct, 8192, nrhs, sc);
+    pl.copy(Prec::F64, Prec::F64, false, ct, 8192, nrhs);
   }
   // backward sweep
   for (int H = h.Hmax - 1; H >= 0; --H) {
@@ -1560,7 +1690,7 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
       }
       ct.push_back(CopyTask{src, c[H] + ht.v_off[g] + m, ht.r[g], nrhs, lds, (int)lv});
     }
-    run_copy(Prec::F64, Prec::F64, false, ct, 256, nrhs, sc);
+    pl.copy(Prec::F64, Prec::F64, false, ct, 256, nrhs);
     GemmBatch g1;
     std::vector<TrsmTask> tu;
     for (int g = 0; g < nb; ++g) {
@@ -1571,8 +1701,8 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
               ht.r[g], -1.0, 1.0);
       tu.push_back(TrsmTask{Sg, c[H] + ht.v_off[g], m, nrhs, ht.n[g], (int)lv, nullptr});
     }
-    g1.run(Prec::F64, false, false, sc);
-    run_trsm(Prec::F64, false, false, false, tu, nrhs, sc);
+    pl.gemm(Prec::F64, g1, false, false);
+    pl.trsm(Prec::F64, false, false, false, tu, nrhs);
     GemmBatch g2;
     for (int g = 0; g < nb; ++g) {
       double* dst;
@@ -1588,9 +1718,9 @@ static void ulv_solve_tree(Handle& h, const double* b, double* x, int nrhs) {
       }
       g2.add1(dst, ldd, ht.n[g], nrhs, ht.Q->as<double>() + ht.q_off[g], ht.n[g], c[H] + ht.v_off[g], (int)lv, ht.n[g]);
     }
-    g2.run(Prec::F64, false, false, sc);
+    pl.gemm(Prec::F64, g2, false, false);
   }
-  H2_CUDA(cudaStreamSynchronize(s));
+  return P;
 }
 
 }  // namespace h2
@@ -1736,6 +1866,7 @@ h2_status h2_factor(h2_handle H, int32_t precision, int32_t spd) {
   return guard([&] {
     Handle& h = H->h;
     h.factored = false;
+    h.plans.clear();
     double t0 = now_ms();
     factor(h, precision, spd);
     h.t_factor_ms = now_ms() - t0;
@@ -1745,24 +1876,50 @@ h2_status h2_factor(h2_handle H, int32_t precision, int32_t spd) {
   });
 }
 
-// Copy a caller vector block (host or device, user order) into tree order.
-static void to_tree(Handle& h, const double* src, int64_t ld, int nrhs, double* dst_tree, Scratch& sc) {
+// Workspaces and plans for nrhs right-hand sides (built on first use; the
+// ULV plan is rebuilt after each factorization).
+static Handle::SolvePlans& solve_plans(Handle& h, int nrhs, bool need_ulv) {
+  auto& sp = h.plans[nrhs];
+  if (!sp) {
+    sp = std::make_shared<Handle::SolvePlans>();
+    sp->nrhs = nrhs;
+    auto mk = [&](size_t e) {
+      auto b = std::make_shared<DBuf>(std::max<size_t>(e, 2) * 8);
+      sp->bufs.push_back(b);
+      return b->as<double>();
+    };
+    size_t NE = (size_t)h.Ntot * nrhs;
+    sp->B = mk(NE);
+    sp->X = mk(NE);
+    sp->R = mk(NE);
+    sp->Uin = mk(NE);
+    sp->Uout = mk(NE);
+    sp->nrm = mk(2 * (size_t)nrhs);
+    sp->mv = build_matvec_plan(h, sp->X, sp->R, nrhs);
+  }
+  if (need_ulv && !sp->ulv) sp->ulv = build_ulv_plan(h, sp->Uin, sp->Uout, nrhs);
+  return *sp;
+}
+
+// Caller block (host or device, caller order, leading dim ld) -> tree order.
+static void to_tree(Handle& h, const double* src, int64_t ld, int nrhs, double* dst_tree, double* stage) {
   const double* d = src;
   if (!is_device_ptr(src)) {
-    double* tmp = (double*)sc.alloc((size_t)ld * nrhs * 8);
-    H2_CUDA(cudaMemcpyAsync(tmp, src, (size_t)ld * nrhs * 8, cudaMemcpyHostToDevice, h.s));
-    d = tmp;
+    H2_CUDA(cudaMemcpy2DAsync(stage, (size_t)h.Ntot * 8, src, (size_t)ld * 8, (size_t)h.Ntot * 8, nrhs,
+                              cudaMemcpyHostToDevice, h.s));
+    d = stage;
+    ld = h.Ntot;
   }
   launch_permute_rows(d, ld, dst_tree, h.Ntot, h.perm.as<int64_t>(), h.Ntot, nrhs, false, h.s);
 }
 
-static void from_tree(Handle& h, const double* src_tree, double* dst, int64_t ld, int nrhs, Scratch& sc) {
+static void from_tree(Handle& h, const double* src_tree, double* dst, int64_t ld, int nrhs, double* stage) {
   if (is_device_ptr(dst)) {
     launch_permute_rows(src_tree, h.Ntot, dst, ld, h.perm.as<int64_t>(), h.Ntot, nrhs, true, h.s);
   } else {
-    double* tmp = (double*)sc.alloc((size_t)ld * nrhs * 8);
-    launch_permute_rows(src_tree, h.Ntot, tmp, ld, h.perm.as<int64_t>(), h.Ntot, nrhs, true, h.s);
-    H2_CUDA(cudaMemcpyAsync(dst, tmp, (size_t)ld * nrhs * 8, cudaMemcpyDeviceToHost, h.s));
+    launch_permute_rows(src_tree, h.Ntot, stage, h.Ntot, h.perm.as<int64_t>(), h.Ntot, nrhs, true, h.s);
+    H2_CUDA(cudaMemcpy2DAsync(dst, (size_t)ld * 8, stage, (size_t)h.Ntot * 8, (size_t)h.Ntot * 8, nrhs,
+                              cudaMemcpyDeviceToHost, h.s));
   }
   H2_CUDA(cudaStreamSynchronize(h.s));
 }
@@ -1774,12 +1931,10 @@ h2_status h2_matvec(h2_handle H, const double* x, double* y, int32_t nrhs, int64
   }
   return guard([&] {
     Handle& h = H->h;
-    Scratch sc(h.s);
-    double* xt = (double*)sc.alloc((size_t)h.Ntot * nrhs * 8);
-    double* yt = (double*)sc.alloc((size_t)h.Ntot * nrhs * 8);
-    to_tree(h, x, ld, nrhs, xt, sc);
-    matvec_tree(h, xt, yt, nrhs);
-    from_tree(h, yt, y, ld, nrhs, sc);
+    auto& sp = solve_plans(h, nrhs, false);
+    to_tree(h, x, ld, nrhs, sp.X, sp.Uin);
+    sp.mv->run(h.s);
+    from_tree(h, sp.R, y, ld, nrhs, sp.Uin);
   });
 }
 
@@ -1796,29 +1951,27 @@ h2_status h2_solve(h2_handle H, const double* b, double* x, int32_t nrhs, int64_
   bool converged = true;
   h2_status st = guard([&] {
     Handle& h = H->h;
-    Scratch sc(h.s);
     const int64_t N = h.Ntot;
-    double* bt = (double*)sc.alloc((size_t)N * nrhs * 8);
-    double* xt = (double*)sc.alloc((size_t)N * nrhs * 8);
-    double* rt = (double*)sc.alloc((size_t)N * nrhs * 8);
-    double* dt = (double*)sc.alloc((size_t)N * nrhs * 8);
-    double* nrm = (double*)sc.alloc((size_t)nrhs * 8 * 2);
-    to_tree(h, b, ld, nrhs, bt, sc);
-    launch_colnorm2(bt, (int)N, nrhs, N, nrm, h.s);
+    const size_t bytes = (size_t)N * nrhs * 8;
+    auto& sp = solve_plans(h, nrhs, true);
+    to_tree(h, b, ld, nrhs, sp.B, sp.Uin);
+    launch_colnorm2(sp.B, (int)N, nrhs, N, sp.nrm, h.s);
     std::vector<double> bn(nrhs), rn(nrhs);
-    H2_CUDA(cudaMemcpyAsync(bn.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
+    H2_CUDA(cudaMemcpyAsync(bn.data(), sp.nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
     H2_CUDA(cudaStreamSynchronize(h.s));
     for (double v : bn)
       if (!std::isfinite(v)) throw StatusError(H2_ERR_NONFINITE, "non-finite right-hand side");
-    ulv_solve_tree(h, bt, xt, nrhs);
+    // x0 = ULV^-1 b
+    H2_CUDA(cudaMemcpyAsync(sp.Uin, sp.B, bytes, cudaMemcpyDeviceToDevice, h.s));
+    sp.ulv->run(h.s);
+    H2_CUDA(cudaMemcpyAsync(sp.X, sp.Uout, bytes, cudaMemcpyDeviceToDevice, h.s));
     int it = 0;
     std::vector<double> rel(nrhs, 0.0);
     while (true) {
-      matvec_tree(h, xt, rt, nrhs);
-      // r = b - A x
-      launch_axpy_cols(rt, bt, (int)N, nrhs, N, N, -1.0, h.s);   // rt = A x - b
-      launch_colnorm2(rt, (int)N, nrhs, N, nrm, h.s);
-      H2_CUDA(cudaMemcpyAsync(rn.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
+      sp.mv->run(h.s);                                               // R = A_H2 X
+      launch_axpy_cols(sp.R, sp.B, (int)N, nrhs, N, N, -1.0, h.s);   // R = A X - b
+      launch_colnorm2(sp.R, (int)N, nrhs, N, sp.nrm, h.s);
+      H2_CUDA(cudaMemcpyAsync(rn.data(), sp.nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
       H2_CUDA(cudaStreamSynchronize(h.s));
       bool ok = true;
       for (int c = 0; c < nrhs; ++c) {
@@ -1830,12 +1983,13 @@ h2_status h2_solve(h2_handle H, const double* b, double* x, int32_t nrhs, int64_
         converged = ok;
         break;
       }
-      // x <- x - ULV^-1 (A x - b)
-      ulv_solve_tree(h, rt, dt, nrhs);
-      launch_axpy_cols(xt, dt, (int)N, nrhs, N, N, -1.0, h.s);
+      // X <- X - ULV^-1 (A X - b)
+      H2_CUDA(cudaMemcpyAsync(sp.Uin, sp.R, bytes, cudaMemcpyDeviceToDevice, h.s));
+      sp.ulv->run(h.s);
+      launch_axpy_cols(sp.X, sp.Uout, (int)N, nrhs, N, N, -1.0, h.s);
       ++it;
     }
-    from_tree(h, xt, x, ld, nrhs, sc);
+    from_tree(h, sp.X, x, ld, nrhs, sp.Uin);
     if (achieved)
       for (int c = 0; c < nrhs; ++c) achieved[c] = rel[c];
     if (iters) *iters = it;

@@ -114,6 +114,93 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmTask* __restrict__ t
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Skinny products (N <= 8 columns: one right-hand side or a few): the 64-wide
+// tile of the GEMM above would waste most of its FMAs, so each CTA streams a
+// 256-row slice of op(A) once and keeps the N columns of op(B) in shared
+// memory.  Non-transposed terms: one thread per row, coalesced along the
+// column.  Transposed terms: one warp per row, lanes along the contiguous
+// column, then a warp reduction.  This is bandwidth-bound by design.
+// ---------------------------------------------------------------------------
+constexpr int GV_ROWS = 256, GV_K = 256, GV_MAXN = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(NT) gemv_kernel(const GemmTask* __restrict__ tasks,
+                                                  const GemmTerm* __restrict__ terms) {
+  const GemmTask tk = tasks[blockIdx.x];
+  const int i0 = blockIdx.y * GV_ROWS;
+  if (i0 >= tk.M) return;
+  const int rows = min(GV_ROWS, tk.M - i0);
+  const int N = tk.N;
+  __shared__ T xs[GV_K][GV_MAXN];
+  __shared__ T yacc[GV_ROWS][GV_MAXN + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < GV_ROWS * (GV_MAXN + 1); e += NT) (&yacc[0][0])[e] = (T)0;
+  for (int t = tk.t0; t < tk.t0 + tk.nt; ++t) {
+    const GemmTerm tm = terms[t];
+    const bool TRA = (tm.flags & 1) != 0, TRB = (tm.flags & 2) != 0;
+    const T* A = reinterpret_cast<const T*>(tm.A);
+    const T* B = reinterpret_cast<const T*>(tm.B);
+    for (int k0 = 0; k0 < tm.K; k0 += GV_K) {
+      const int kc = min(GV_K, tm.K - k0);
+      __syncthreads();
+      for (int e = tid; e < kc * N; e += NT) {
+        int k = e % kc, c = e / kc;
+        xs[k][c] = TRB ? B[c + (long long)(k0 + k) * tm.ldb] : B[(k0 + k) + (long long)c * tm.ldb];
+      }
+      __syncthreads();
+      if (!TRA) {
+        if (tid < rows) {
+          T acc[GV_MAXN];
+#pragma unroll
+          for (int c = 0; c < GV_MAXN; ++c) acc[c] = (T)0;
+          const T* a = A + (i0 + tid) + (long long)k0 * tm.lda;
+#pragma unroll 4
+          for (int k = 0; k < kc; ++k) {
+            T v = a[(long long)k * tm.lda];
+#pragma unroll
+            for (int c = 0; c < GV_MAXN; ++c)
+              if (c < N) acc[c] = fma(v, xs[k][c], acc[c]);
+          }
+#pragma unroll
+          for (int c = 0; c < GV_MAXN; ++c)
+            if (c < N) yacc[tid][c] += acc[c];
+        }
+      } else {
+        for (int r = warp; r < rows; r += NT / 32) {
+          T acc[GV_MAXN];
+#pragma unroll
+          for (int c = 0; c < GV_MAXN; ++c) acc[c] = (T)0;
+          const T* a = A + k0 + (long long)(i0 + r) * tm.lda;
+          for (int k = lane; k < kc; k += 32) {
+            T v = a[k];
+#pragma unroll
+            for (int c = 0; c < GV_MAXN; ++c)
+              if (c < N) acc[c] = fma(v, xs[k][c], acc[c]);
+          }
+#pragma unroll
+          for (int c = 0; c < GV_MAXN; ++c) {
+            T v = acc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0 && c < N) yacc[r][c] += v;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  T* C = reinterpret_cast<T*>(tk.C);
+  const T* Cin = reinterpret_cast<const T*>(tk.Cin);
+  for (int e = tid; e < rows * N; e += NT) {
+    int i = e % rows, c = e / rows;
+    T v = (T)tk.alpha * yacc[i][c];
+    if (Cin != nullptr && tk.beta != 0.0) v += (T)tk.beta * Cin[(i0 + i) + (long long)c * tk.ldcin];
+    C[(i0 + i) + (long long)c * tk.ldc] = v;
+  }
+}
+
 template <typename T, bool F64IN>
 void dispatch(const GemmTask* d_tasks, const GemmTerm* d_terms, dim3 grid, cudaStream_t s) {
   gemm_kernel<T, F64IN><<<grid, NT, 0, s>>>(d_tasks, d_terms);
@@ -124,6 +211,14 @@ void dispatch(const GemmTask* d_tasks, const GemmTerm* d_terms, dim3 grid, cudaS
 void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
                  int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64) {
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return;
+  if (maxN <= GV_MAXN && !inputs_f64) {
+    dim3 g(ntasks, (maxM + GV_ROWS - 1) / GV_ROWS);
+    ProfScope ps(p == Prec::F64 ? "gemv_f64" : "gemv_f32", s);
+    if (p == Prec::F64) gemv_kernel<double><<<g, NT, 0, s>>>(d_tasks, d_terms);
+    else gemv_kernel<float><<<g, NT, 0, s>>>(d_tasks, d_terms);
+    H2_LAUNCH_CHECK();
+    return;
+  }
   int tiles = ((maxM + BM - 1) / BM) * ((maxN + BN - 1) / BN);
   dim3 grid(ntasks, tiles);
   ProfScope ps(p == Prec::F64 ? "gemm_f64" : "gemm_f32", s);
