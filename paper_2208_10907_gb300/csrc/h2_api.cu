@@ -295,12 +295,16 @@ static void run_interp(Prec p, const std::vector<InterpTask>& v, Scratch& sc) {
 // A fixed sequence of batched launches with device-resident task arrays,
 // replayed without host work; captured once into a CUDA graph.
 struct Op {
-  int kind;             // 0 gemm, 1 trsm, 2 copy, 3 axpy-free marker
+  int kind;             // 0 gemm, 1 trsm, 2 copy, 3 symmetric near pairs, 4 gather partials
   Prec p, p2;
   bool f1, f2, f3;
   const void* tasks;
   const void* terms;
   int n, a, b;
+  const char* tag;
+  const double* x;      // kinds 3, 4
+  double* y;
+  long long ld;
 };
 
 struct Plan {
@@ -335,6 +339,7 @@ struct Plan {
     o.n = (int)gb.tasks.size();
     o.a = gb.maxM;
     o.b = gb.maxN;
+    o.tag = cur_tag;
     ops.push_back(o);
   }
   void trsm(Prec p, bool lower, bool unit, bool tr, const std::vector<TrsmTask>& v, int maxrhs) {
@@ -349,6 +354,7 @@ struct Plan {
     o.tasks = up(v);
     o.n = (int)v.size();
     o.a = maxrhs;
+    o.tag = cur_tag;
     ops.push_back(o);
   }
   void copy(Prec a, Prec b, bool tr, const std::vector<CopyTask>& v, int mr, int mc) {
@@ -363,14 +369,48 @@ struct Plan {
     o.n = (int)v.size();
     o.a = mr;
     o.b = mc;
+    o.tag = cur_tag;
+    ops.push_back(o);
+  }
+  const char* cur_tag = nullptr;
+  void tag(const char* t) { cur_tag = t; }
+  void symv(const std::vector<SymPairTask>& v, const double* x, long long ldx, double* part, int nrhs) {
+    Op o{};
+    o.kind = 3;
+    o.tasks = up(v);
+    o.n = (int)v.size();
+    o.x = x;
+    o.y = part;
+    o.ld = ldx;
+    o.a = nrhs;
+    o.tag = cur_tag;
+    ops.push_back(o);
+  }
+  void gather(const std::vector<GatherTask>& v, const std::vector<long long>& offs, const double* part, double* y,
+              long long ldy, int nrhs) {
+    Op o{};
+    o.kind = 4;
+    o.tasks = up(v);
+    o.terms = up(offs);
+    o.n = (int)v.size();
+    o.x = part;
+    o.y = y;
+    o.ld = ldy;
+    o.a = nrhs;
+    o.tag = cur_tag;
     ops.push_back(o);
   }
   void issue(cudaStream_t st) const {
     for (const Op& o : ops) {
+      prof_tag(o.tag);
       if (o.kind == 0) launch_gemm(o.p, (const GemmTask*)o.tasks, (const GemmTerm*)o.terms, o.n, o.a, o.b, st);
       else if (o.kind == 1) launch_trsm(o.p, o.f1, o.f2, o.f3, (const TrsmTask*)o.tasks, o.n, o.a, st);
       else if (o.kind == 2) launch_copy(o.p, o.p2, o.f1, (const CopyTask*)o.tasks, o.n, o.a, o.b, st);
+      else if (o.kind == 3) launch_symv_pairs((const SymPairTask*)o.tasks, o.n, o.x, o.ld, o.y, o.a, st);
+      else if (o.kind == 4)
+        launch_gather_parts((const GatherTask*)o.tasks, o.n, (const long long*)o.terms, o.x, o.y, o.ld, o.a, st);
     }
+    prof_tag(nullptr);
   }
   // replay: through the captured graph when profiling is off, else launch by
   // launch (so each kernel is timed on its own)
@@ -788,7 +828,50 @@ static PlanP build_matvec_plan(Handle& h, const double* x, double* y, int nrhs) 
   Plan& pl = *P;
   const int64_t ld = h.Ntot;
   // near part (leaf dense blocks): y_I = sum_J A_IJ x_J
-  {
+  pl.tag("mv_near");
+  if (nrhs <= 2) {
+    // each stored block read once: partials for both boxes, then a fixed-order sum
+    std::vector<SymPairTask> st;
+    std::vector<size_t> pofs(h.leaf_pair_ptr.back(), 0);   // partial offset seen by pair (g, q)
+    long long tot = 0;
+    for (size_t g = 0; g < h.leaf_ref.size(); ++g)
+      for (size_t q = 0; q < h.leaf_near[g].size(); ++q) {
+        int j = h.leaf_near[g][q];
+        if ((int)g > j) continue;
+        SymPairTask t;
+        t.A = h.leaf_blk.as<double>() + h.leaf_blk_off[h.leaf_pair_ptr[g] + q];
+        t.nI = h.leaf_n[g];
+        t.nJ = h.leaf_n[j];
+        t.lda = h.leaf_n[g];
+        t.sI = h.leaf_s[g];
+        t.sJ = h.leaf_s[j];
+        t.uo = tot;
+        tot += (long long)t.nI * nrhs;
+        t.vo = tot;
+        tot += (long long)t.nJ * nrhs;
+        pofs[h.leaf_pair_ptr[g] + q] = (size_t)t.uo;
+        if ((int)g != j) {
+          const auto& nl = h.leaf_near[j];
+          size_t qq = std::find(nl.begin(), nl.end(), (int)g) - nl.begin();
+          pofs[h.leaf_pair_ptr[j] + qq] = (size_t)t.vo;
+        }
+        st.push_back(t);
+      }
+    double* part = pl.work((size_t)tot);
+    std::vector<GatherTask> gt;
+    std::vector<long long> offs;
+    for (size_t g = 0; g < h.leaf_ref.size(); ++g) {
+      GatherTask t;
+      t.s = h.leaf_s[g];
+      t.n = h.leaf_n[g];
+      t.p0 = (int)offs.size();
+      for (size_t q = 0; q < h.leaf_near[g].size(); ++q) offs.push_back((long long)pofs[h.leaf_pair_ptr[g] + q]);
+      t.np = (int)(offs.size() - t.p0);
+      gt.push_back(t);
+    }
+    pl.symv(st, x, ld, part, nrhs);
+    pl.gather(gt, offs, part, y, ld, nrhs);
+  } else {
     GemmBatch gb;
     for (size_t g = 0; g < h.leaf_ref.size(); ++g) {
       std::vector<GemmTerm> ts;
@@ -801,6 +884,7 @@ static PlanP build_matvec_plan(Handle& h, const double* x, double* y, int nrhs) 
     }
     pl.gemm(Prec::F64, gb, false, false);
   }
+  pl.tag("mv_far");
   if (h.Hmax == 0) return P;
   // upward pass
   std::vector<double*> xh(h.Hmax), yh(h.Hmax);
@@ -1104,6 +1188,7 @@ static void factor(Handle& h, int precision, int spd) {
       return -1;
     };
     // ---------------- 1. fill-ins (Sec. III-B) --------------------------
+    prof_tag("fillin");
     std::vector<int> has_lu(nb, 0);
     for (int g = 0; g < nb; ++g) has_lu[g] = ht.near[g].size() > 1;
     // scratch slots of maxn x maxn per box (V blocks are n_I x n_K)
@@ -1187,6 +1272,7 @@ static void factor(Handle& h, int precision, int spd) {
       }
     }
     // ---------------- 2. basis with fill-ins (eq. fillu) ---------------
+    prof_tag("basis");
     double* G = (double*)sc.alloc(NN * 8);
     {
       std::vector<CopyTask> ct;
@@ -1402,6 +1488,7 @@ static void factor(Handle& h, int precision, int spd) {
       return (char*)rt.A->p + (ro + co * rt.n) * ws;
     };
     // ---------------- 3. projection (eq. rs, eq. ss) -------------------
+    prof_tag("proj");
     void* Sw = sc.alloc(NN * ws);
     {
       GemmBatch g1, g2;
@@ -1467,6 +1554,7 @@ static void factor(Handle& h, int precision, int spd) {
       }
     }
     // ---------------- 4. partial LU of S^RR (eq. lu) -------------------
+    prof_tag("elim");
     ht.S = std::make_shared<DBuf>(NN * 8);
     {
       std::vector<CopyTask> ct;
@@ -1530,6 +1618,7 @@ static void factor(Handle& h, int precision, int spd) {
     H2_CUDA(cudaStreamSynchronize(s));
     if (hinfo != 0) throw StatusError(H2_ERR_SINGULAR, "zero pivot in a redundant-block LU");
     // ---------------- 5. next height: T = blockdiag(W_a, W_b) ---------
+    prof_tag("merge");
     if (up) {
       std::vector<size_t> to(up->nb + 1, 0);
       for (int pg = 0; pg < up->nb; ++pg) to[pg + 1] = to[pg] + (size_t)up->n[pg] * up->n[pg];
@@ -1559,6 +1648,7 @@ static void factor(Handle& h, int precision, int spd) {
     h.level_ms.push_back(now_ms() - t0);
   }
   // roots
+  prof_tag("root");
   for (auto& pb : h.probs) {
     Root& rt = pb.root;
     if (rt.n == 0) continue;
@@ -1568,6 +1658,7 @@ static void factor(Handle& h, int precision, int spd) {
     root_factor(h, rt, spd);
     rt.A.reset();
   }
+  prof_tag(nullptr);
   H2_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1598,6 +1689,7 @@ static PlanP build_ulv_plan(Handle& h, const double* b, double* x, int nrhs) {
     pl.copy(Prec::F64, Prec::F64, false, ct, 8192, nrhs);
   }
   // forward sweep
+  pl.tag("ulv_fwd");
   for (int H = 0; H < h.Hmax; ++H) {
     Height& ht = h.hs[H];
     const int nb = ht.nb;
@@ -1652,6 +1744,7 @@ static PlanP build_ulv_plan(Handle& h, const double* b, double* x, int nrhs) {
     pl.copy(Prec::F64, Prec::F64, false, ct, 256, nrhs);
   }
   // root solves
+  pl.tag("ulv_root");
   {
     GemmBatch gb;
     for (size_t p = 0; p < h.probs.size(); ++p) {
@@ -1669,6 +1762,7 @@ static PlanP build_ulv_plan(Handle& h, const double* b, double* x, int nrhs) {
     pl.copy(Prec::F64, Prec::F64, false, ct, 8192, nrhs);
   }
   // backward sweep
+  pl.tag("ulv_bwd");
   for (int H = h.Hmax - 1; H >= 0; --H) {
     Height& ht = h.hs[H];
     const int nb = ht.nb;

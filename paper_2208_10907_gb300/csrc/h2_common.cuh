@@ -175,6 +175,17 @@ struct InterpTask {    // P (n x r) from piv, T = R11^-1 R12 (r x (n-r), ld ldt)
   int n, r, ldt;
 };
 
+struct SymPairTask {   // stored block (I, J), I <= J: partials u (box I) and v (box J)
+  const void* A;
+  int nI, nJ, lda;
+  long long sI, sJ;    // tree-order starts of the boxes' rows in x
+  long long uo, vo;    // element offsets of u (nI x nrhs) and v (nJ x nrhs) in the partial buffer
+};
+struct GatherTask {    // y[s : s+n] = sum of partials p0 .. p0+np-1
+  long long s;
+  int n, p0, np;
+};
+
 // ---------------------------------------------------------------------------
 // Launch wrappers (defined in the k_*.cu files).  Each takes a device array
 // of tasks plus a host-side count and maxima for the grid.
@@ -206,6 +217,10 @@ void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ld
 void launch_fill_eye(Prec p, void* A, int n, int ld, cudaStream_t s);
 void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int k0, int k1,
                        int col_begin, int col_end, cudaStream_t s);
+void launch_symv_pairs(const SymPairTask* d, int ntasks, const double* x, int64_t ldx, double* part, int nrhs,
+                       cudaStream_t s);
+void launch_gather_parts(const GatherTask* d, int ntasks, const long long* offs, const double* part, double* y,
+                         int64_t ldy, int nrhs, cudaStream_t s);
 void launch_logdet_lu(const LuTask* d, int ntasks, double* out_log, double* out_sign,
                       bool cholesky, cudaStream_t s);
 

@@ -12,6 +12,8 @@ void prof_note(double flops, double bytes) {
   prof().next_bytes += bytes;
 }
 
+void prof_tag(const char* tag) { prof().tag = tag ? tag : ""; }
+
 void Prof::resolve() {
   for (auto& q : pending) {
     float ms = 0.f;
@@ -32,6 +34,7 @@ void Prof::reset() {
 
 ProfScope::ProfScope(const char* n, cudaStream_t st) : name(n), s(st) {
   Prof& p = prof();
+  if (!p.tag.empty()) name += "@" + p.tag;
   KStat& k = p.stats[name];
   k.launches += 1;
   k.flops += p.next_flops;

@@ -25,6 +25,7 @@ struct Prof {
   };
   std::vector<Pending> pending;
   double next_flops = 0.0, next_bytes = 0.0;
+  std::string tag;                 // call-site tag appended to kernel names
   long long total_launches = 0;
   void resolve();
   void reset();
@@ -32,9 +33,10 @@ struct Prof {
 
 Prof& prof();
 void prof_note(double flops, double bytes);
+void prof_tag(const char* tag);   // nullptr clears
 
 struct ProfScope {
-  const char* name;
+  std::string name;
   cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
   ProfScope(const char* n, cudaStream_t st);
