@@ -47,7 +47,8 @@ typedef enum {
   H2_ERR_NOT_CONVERGED = 7, /* refinement stopped at max_iter above the target  */
   H2_ERR_DEVICE = 8,        /* CUDA error (message in h2_last_error)            */
   H2_ERR_STATE = 9,         /* call out of order (e.g. solve before factor)     */
-  H2_ERR_NOT_SPD = 10       /* Cholesky pivot <= 0 in the SPD path              */
+  H2_ERR_NOT_SPD = 10,      /* Cholesky pivot <= 0 in the SPD path              */
+  H2_ERR_TIMEOUT = 11       /* a bounded device-side wait gave up               */
 } h2_status;
 
 /* Kernel functions (Sec. IV: Laplace Green's function; Sec. V: Yukawa).

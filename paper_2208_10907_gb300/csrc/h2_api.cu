@@ -1660,6 +1660,8 @@ static void factor(Handle& h, int precision, int spd) {
   }
   prof_tag(nullptr);
   H2_CUDA(cudaStreamSynchronize(s));
+  if (W == Prec::F32 && tc_error_flag_read_and_clear(s))
+    throw StatusError(H2_ERR_TIMEOUT, "a tensor-core completion wait gave up");
 }
 
 // -------------------------------------------------------------- solve ----

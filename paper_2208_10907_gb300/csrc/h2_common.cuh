@@ -221,6 +221,7 @@ void launch_symv_pairs(const SymPairTask* d, int ntasks, const double* x, int64_
                        cudaStream_t s);
 void launch_gather_parts(const GatherTask* d, int ntasks, const long long* offs, const double* part, double* y,
                          int64_t ldy, int nrhs, cudaStream_t s);
+int tc_error_flag_read_and_clear(cudaStream_t s);
 void launch_logdet_lu(const LuTask* d, int ntasks, double* out_log, double* out_sign,
                       bool cholesky, cudaStream_t s);
 

@@ -208,6 +208,19 @@ void dispatch(const GemmTask* d_tasks, const GemmTerm* d_terms, dim3 grid, cudaS
 
 }  // namespace
 
+void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, int ntasks, int maxM, int maxN,
+                    cudaStream_t s);
+
+// FP32-class products go to the tcgen05 split-3xTF32 kernel unless H2_TC=0.
+static bool tc_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("H2_TC");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v == 1;
+}
+
 void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
                  int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64) {
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return;
@@ -217,6 +230,10 @@ void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
     if (p == Prec::F64) gemv_kernel<double><<<g, NT, 0, s>>>(d_tasks, d_terms);
     else gemv_kernel<float><<<g, NT, 0, s>>>(d_tasks, d_terms);
     H2_LAUNCH_CHECK();
+    return;
+  }
+  if (p == Prec::F32 && !inputs_f64 && tc_enabled() && maxM >= 32 && maxN >= 32) {
+    launch_gemm_tc(d_tasks, d_terms, ntasks, maxM, maxN, s);
     return;
   }
   int tiles = ((maxM + BM - 1) / BM) * ((maxN + BN - 1) / BN);

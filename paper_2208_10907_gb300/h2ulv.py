@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libh2ulv.so")
 
 H2_OK, H2_ERR_ARG, H2_ERR_NONFINITE, H2_ERR_OOM, H2_ERR_BUDGET = 0, 1, 2, 3, 4
 H2_ERR_SINGULAR, H2_ERR_RANK_CAP, H2_ERR_NOT_CONVERGED, H2_ERR_DEVICE = 5, 6, 7, 8
-H2_ERR_STATE, H2_ERR_NOT_SPD = 9, 10
+H2_ERR_STATE, H2_ERR_NOT_SPD, H2_ERR_TIMEOUT = 9, 10, 11
 H2_K_LAPLACE, H2_K_YUKAWA, H2_K_MATERN32 = 0, 1, 2
 H2_FP64, H2_MIXED = 0, 1
 KERNEL_KIND = {"laplace": H2_K_LAPLACE, "yukawa": H2_K_YUKAWA, "matern32": H2_K_MATERN32}
