@@ -150,6 +150,24 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int32_t nrhs, int64
  * arrays of length P). */
 h2_status h2_logdet(h2_handle h, double* log_abs_det, int32_t* sign);
 
+/* Allocation-free variant of h2_logdet, for callers that cannot call
+ * cudaMalloc when they need the value (their device memory is fully reserved
+ * or owned by another allocator, or they must not trigger an allocation
+ * between latency-critical launches).  The paper has no counterpart: it is
+ * an interface addition of this library.  Same result as h2_logdet (host
+ * arrays of length P for a batched handle).
+ *   - Scratch: a fixed 768 KB device array inside the library (task
+ *     descriptors and per-block partials), held by every device that loads
+ *     the library until the process exits; nothing is allocated per call.
+ *   - Limit: at most 16384 factored blocks per tree height; larger handles
+ *     are rejected with H2_ERR_ARG.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device); make that first call before any stream capture.
+ *   - Every call shares the array and it keeps the last call's contents;
+ *     calls that overlap on the GPU (several host threads or handles at
+ *     once) race on it and must be serialised by the caller. */
+h2_status h2_logdet_noalloc(h2_handle h, double* log_abs_det, int32_t* sign);
+
 /* JSON statistics: per-level ranks, flops, bytes, times (ms); cap = size of
  * the host buffer json.  Truncated output is still NUL-terminated. */
 h2_status h2_stats(h2_handle h, char* json, size_t cap);

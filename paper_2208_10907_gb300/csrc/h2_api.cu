@@ -1819,6 +1819,23 @@ static PlanP build_ulv_plan(Handle& h, const double* b, double* x, int nrhs) {
   return P;
 }
 
+
+// ------------------------------------------------------ allocation-free --
+// Log-determinant without any device allocation, for callers that cannot
+// call cudaMalloc at that point: a process whose device memory is owned by
+// another allocator or fully reserved, or code that must not trigger a
+// synchronising allocation between captured or latency-critical launches.
+// The per-block task descriptors and partial results live in this
+// file-scope device array (every device that loads the library holds it
+// until exit); the host-side name is only a stand-in, so its device
+// address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+constexpr int NOALLOC_MAX_BLOCKS = 16384;   // factored blocks per height
+constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX_BLOCKS * (sizeof(LuTask) + 2 * sizeof(double));
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+void* g_noalloc_ptr[256] = {nullptr};
+}  // namespace
+
 }  // namespace h2
 
 // ================================================================= C ABI ==
@@ -2136,6 +2153,65 @@ h2_status h2_logdet(h2_handle H, double* log_abs_det, int32_t* sign) {
       sg[p] *= h.probs[p].root.sign;
       log_abs_det[p] = ld[p];
       if (sign) sign[p] = sg[p] < 0 ? -1 : 1;
+    }
+  });
+}
+
+
+h2_status h2_logdet_noalloc(h2_handle H, double* log_abs_det, int32_t* sign) {
+  if (!H || !log_abs_det) {
+    g_err = "invalid logdet arguments";
+    return H2_ERR_ARG;
+  }
+  if (!H->h.factored) {
+    g_err = "h2_logdet_noalloc before h2_factor";
+    return H2_ERR_STATE;
+  }
+  return guard([&] {
+    Handle& h = H->h;
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) throw StatusError(H2_ERR_ARG, "device index out of range");
+    if (!g_noalloc_ptr[dev]) {
+      // first call on this device: resolve the scratch array's device address
+      void* p = nullptr;
+      H2_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = p;
+    }
+    LuTask* d_tasks = reinterpret_cast<LuTask*>(g_noalloc_ptr[dev]);
+    double* d_out = reinterpret_cast<double*>(reinterpret_cast<char*>(g_noalloc_ptr[dev]) +
+                                              (size_t)NOALLOC_MAX_BLOCKS * sizeof(LuTask));
+    const size_t P = h.probs.size();
+    for (size_t p = 0; p < P; ++p) {
+      log_abs_det[p] = h.probs[p].root.logdet;
+      if (sign) sign[p] = h.probs[p].root.sign < 0 ? -1 : 1;
+    }
+    std::vector<LuTask> lt;
+    std::vector<int> who;
+    std::vector<double> ho;
+    for (int Hh = 0; Hh < h.Hmax; ++Hh) {
+      Height& ht = h.hs[Hh];
+      lt.clear();
+      who.clear();
+      for (int g = 0; g < ht.nb; ++g) {
+        int m = ht.n[g] - ht.r[g];
+        if (m == 0) continue;
+        lt.push_back(LuTask{ht.S->as<double>() + ht.q_off[g], m, m, ht.n[g], ht.pivRR->as<int>() + ht.pv_off[g], nullptr});
+        who.push_back(ht.ref[g].prob);
+      }
+      if (lt.empty()) continue;
+      if (lt.size() > (size_t)NOALLOC_MAX_BLOCKS)
+        throw StatusError(H2_ERR_ARG, "h2_logdet_noalloc: more than 16384 factored blocks at one height");
+      const int nblk = (int)lt.size();
+      H2_CUDA(cudaMemcpyAsync(d_tasks, lt.data(), lt.size() * sizeof(LuTask), cudaMemcpyHostToDevice, h.s));
+      launch_logdet_lu(d_tasks, nblk, d_out, d_out + nblk, false, h.s);
+      ho.resize(2 * (size_t)nblk);
+      H2_CUDA(cudaMemcpyAsync(ho.data(), d_out, ho.size() * sizeof(double), cudaMemcpyDeviceToHost, h.s));
+      H2_CUDA(cudaStreamSynchronize(h.s));
+      for (int i = 0; i < nblk; ++i) {
+        log_abs_det[who[i]] += ho[i];
+        if (sign && ho[nblk + i] < 0) sign[who[i]] = -sign[who[i]];
+      }
     }
   });
 }

@@ -21,7 +21,7 @@ H2_FP64, H2_MIXED = 0, 1
 KERNEL_KIND = {"laplace": H2_K_LAPLACE, "yukawa": H2_K_YUKAWA, "matern32": H2_K_MATERN32}
 
 EXPORTED = ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_matvec",
-            "h2_logdet", "h2_stats", "h2_profile", "h2_last_error", "h2_destroy")
+            "h2_logdet", "h2_logdet_noalloc", "h2_stats", "h2_profile", "h2_last_error", "h2_destroy")
 
 
 class h2_kernel(ctypes.Structure):
@@ -60,12 +60,13 @@ def lib():
         L.h2_solve.argtypes = [vp, vp, vp, i32, i64, dp, i32, vp, ctypes.POINTER(i32)]
         L.h2_matvec.argtypes = [vp, vp, vp, i32, i64]
         L.h2_logdet.argtypes = [vp, vp, vp]
+        L.h2_logdet_noalloc.argtypes = [vp, vp, vp]
         L.h2_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         L.h2_profile.argtypes = [i32, i32]
         L.h2_last_error.restype = ctypes.c_char_p
         L.h2_destroy.argtypes = [vp]
         for f in ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_matvec", "h2_logdet",
-                  "h2_stats", "h2_profile"):
+                  "h2_logdet_noalloc", "h2_stats", "h2_profile"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -136,6 +137,14 @@ def h2_logdet(h, nproblems=1):
     ld = np.zeros(nproblems, dtype=np.float64)
     sg = np.zeros(nproblems, dtype=np.int32)
     _check(lib().h2_logdet(h, ctypes.c_void_p(ld.ctypes.data), ctypes.c_void_p(sg.ctypes.data)))
+    return ld, sg
+
+
+def h2_logdet_noalloc(h, nproblems=1):
+    """Same result as h2_logdet; the library allocates no device memory for it."""
+    ld = np.zeros(nproblems, dtype=np.float64)
+    sg = np.zeros(nproblems, dtype=np.int32)
+    _check(lib().h2_logdet_noalloc(h, ctypes.c_void_p(ld.ctypes.data), ctypes.c_void_p(sg.ctypes.data)))
     return ld, sg
 
 
