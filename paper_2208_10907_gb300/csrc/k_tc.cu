@@ -5,15 +5,18 @@
 // A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 in tensor memory, which keeps
 // close to FP32 accuracy (the dropped A_lo B_lo term is ~2^-22 relative).
 //
-// One CTA computes a 128 x 128 output tile of one task.  Operands are
-// staged by the CTA itself (per-term transposition, bounds and the hi/lo
-// split happen in the load path) into the canonical no-swizzle K-major
-// shared-memory layout: 8-row x 16-byte core matrices, core matrices
-// adjacent along K at LBO = 128 bytes, 8-row groups at SBO = (BK/4)*128.
-// One elected thread issues tcgen05.mma (kind::tf32, M = 128, N = 128,
-// K = 8 per instruction) into a 128-column TMEM accumulator; completion is
-// tracked with tcgen05.commit on an mbarrier whose waits are bounded.  The
-// epilogue reads TMEM with tcgen05.ld.32x32b.
+// One CTA computes a 128 x 256 output tile of one task (MMA N sized to the
+// task, a multiple of 16).  Operands are staged by the CTA itself
+// (per-term transposition, bounds and the hi/lo split happen in the load
+// path) into the canonical no-swizzle K-major shared-memory layout: 8-row x
+// 16-byte core matrices, adjacent along K at LBO = 128 bytes, 8-row groups
+// at SBO = (BK/4)*128; each thread writes whole 16-byte core-matrix rows.
+// Two shared-memory stages and a register prefetch of the next K-chunk
+// overlap the global loads with the tensor core.  One elected thread issues
+// tcgen05.mma (kind::tf32, M = 128, K = 8 per instruction) into a
+// 256-column TMEM accumulator; completion is tracked per stage with
+// tcgen05.commit on mbarriers whose waits are bounded.  The epilogue reads
+// TMEM with tcgen05.ld.32x32b.
 #include "h2_common.cuh"
 #include "h2_prof.h"
 
@@ -21,18 +24,12 @@ namespace h2 {
 
 namespace {
 
-constexpr int TM = 128, TN = 128, BK = 32, NTH = 256;
+constexpr int TM = 128, BK = 32, NTH = 256;
 constexpr int SBO = (BK / 4) * 128;                // bytes between 8-row groups
-constexpr int TILE_BYTES = TM * BK * 4;            // one operand tile (A or B), 16 KB
 constexpr long long SPIN_LIMIT = 1ll << 26;        // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// byte offset of element (row, k) in a canonical no-swizzle K-major tile
-__device__ __forceinline__ uint32_t kmaj_off(int row, int k) {
-  return (uint32_t)((row & 7) * 16 + (row >> 3) * SBO + (k >> 2) * 128 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -42,17 +39,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;          // stride byte offset (8-row groups)
   d |= (uint64_t)1 << 46;                              // descriptor version (sm_100 family)
   // base offset 0, lbo mode 0, layout type 0 = no swizzle
-  return d;
-}
-
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
-__device__ __forceinline__ uint32_t instr_desc() {
-  uint32_t d = 0;
-  d |= 1u << 4;                 // c_format = F32
-  d |= 2u << 7;                 // a_format = TF32
-  d |= 2u << 10;                // b_format = TF32
-  d |= (uint32_t)(TN >> 3) << 17;
-  d |= (uint32_t)(TM >> 4) << 24;
   return d;
 }
 
@@ -90,40 +76,101 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-template <typename TIN>
-__device__ __forceinline__ float ldg(const void* p, long long idx) {
-  return (float)reinterpret_cast<const TIN*>(p)[idx];
+
+// Staging: an operand tile is R rows x BK k; its 16-byte units (one row, 4
+// consecutive k) are distributed so that each thread owns whole units and
+// writes them with one 16-byte shared store.  Two mappings: "row-fast"
+// (consecutive lanes take consecutive rows; global loads coalesce when the
+// operand is contiguous along rows) and "k-fast" (8 lanes cover one row's 32
+// k; loads coalesce when the operand is contiguous along k).
+template <int R>
+struct Stage {
+  static constexpr int UNITS = R * (BK / 4);
+  static constexpr int PER = UNITS / NTH;      // units per thread
+  float v[PER][4];
+};
+
+// element (row, k) of op(X) with X column-major: rowmajor_k = true means
+// op(X)(row, k) = X[k + row*ld] (contiguous along k), else X[row + k*ld]
+template <int R>
+__device__ __forceinline__ void stage_load(Stage<R>& st, const float* X, long long ld, bool contig_k, int row0,
+                                           int rows, int k0, int K) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < Stage<R>::PER; ++q) {
+    const int u = tid + q * NTH;
+    int row, kc;
+    if (contig_k) { kc = u & 7; row = u >> 3; } else { row = u % R; kc = u / R; }
+    const int gr = row0 + row;
+    const int gk = k0 + kc * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float v = 0.f;
+      if (gr < rows && gk + j < K) v = contig_k ? X[(gk + j) + (long long)gr * ld] : X[gr + (long long)(gk + j) * ld];
+      st.v[q][j] = v;
+    }
+  }
 }
 
-template <typename TIN>
+template <int R>
+__device__ __forceinline__ void stage_store(const Stage<R>& st, bool contig_k, unsigned char* hi, unsigned char* lo) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < Stage<R>::PER; ++q) {
+    const int u = tid + q * NTH;
+    int row, kc;
+    if (contig_k) { kc = u & 7; row = u >> 3; } else { row = u % R; kc = u / R; }
+    const uint32_t o = (uint32_t)((row & 7) * 16 + (row >> 3) * SBO + kc * 128);
+    float4 h, l;
+    h.x = tf32_hi(st.v[q][0]); l.x = st.v[q][0] - h.x;
+    h.y = tf32_hi(st.v[q][1]); l.y = st.v[q][1] - h.y;
+    h.z = tf32_hi(st.v[q][2]); l.z = st.v[q][2] - h.z;
+    h.w = tf32_hi(st.v[q][3]); l.w = st.v[q][3] - h.w;
+    *reinterpret_cast<float4*>(hi + o) = h;
+    *reinterpret_cast<float4*>(lo + o) = l;
+  }
+}
+
+constexpr int TNB = 256;                              // output tile columns (TMEM columns)
+constexpr int ABYTES = TM * BK * 4, BBYTES = TNB * BK * 4;
+constexpr int STAGE_BYTES = 2 * ABYTES + 2 * BBYTES;  // hi + lo of A and B
+constexpr int NSTAGE = 2;
+
+__device__ __forceinline__ uint32_t instr_desc_n(int n_mma) {
+  uint32_t d = 0;
+  d |= 1u << 4;
+  d |= 2u << 7;
+  d |= 2u << 10;
+  d |= (uint32_t)(n_mma >> 3) << 17;
+  d |= (uint32_t)(TM >> 4) << 24;
+  return d;
+}
+
 __global__ void __launch_bounds__(NTH, 1) tc_gemm_kernel(const GemmTask* __restrict__ tasks,
                                                          const GemmTerm* __restrict__ terms, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  // 4 operand tiles (A_hi, A_lo, B_hi, B_lo), 1024-byte aligned
   unsigned char* base = smem + ((1024 - (smem_u32(smem) & 1023)) & 1023);
-  unsigned char* sAhi = base;
-  unsigned char* sAlo = base + TILE_BYTES;
-  unsigned char* sBhi = base + 2 * TILE_BYTES;
-  unsigned char* sBlo = base + 3 * TILE_BYTES;
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t mbar[NSTAGE];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
 
   const GemmTask tk = tasks[blockIdx.x];
   const int tiles_m = (tk.M + TM - 1) / TM;
-  const int tiles_n = (tk.N + TN - 1) / TN;
+  const int tiles_n = (tk.N + TNB - 1) / TNB;
   const int tile = blockIdx.y;
   if (tile >= tiles_m * tiles_n) return;
-  const int i0 = (tile % tiles_m) * TM, j0 = (tile / tiles_m) * TN;
+  const int i0 = (tile % tiles_m) * TM, j0 = (tile / tiles_m) * TNB;
+  const int ncols = min(TNB, tk.N - j0);
+  const int n_mma = ((ncols + 15) / 16) * 16;          // MMA N: multiple of 16, <= 256
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TN));
+                 "r"(TNB));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    mbar_init(&mbar, 1);
+    for (int q = 0; q < NSTAGE; ++q) mbar_init(&mbar[q], 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -131,83 +178,120 @@ __global__ void __launch_bounds__(NTH, 1) tc_gemm_kernel(const GemmTask* __restr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = instr_desc();
-  uint32_t phase = 0;
-  bool first = true;
+  const uint32_t idesc = instr_desc_n(n_mma);
 
-  for (int t = tk.t0; t < tk.t0 + tk.nt && !s_fail; ++t) {
-    const GemmTerm tm = terms[t];
-    const bool TRA = (tm.flags & 1) != 0, TRB = (tm.flags & 2) != 0;
-    for (int k0 = 0; k0 < tm.K; k0 += BK) {
-      // ---- stage op(A)[i0:i0+128, k0:k0+32] and op(B)^T[j0:j0+128, k0:k0+32]
-      for (int e = tid; e < TM * BK; e += NTH) {
-        int r, k;
-        if (!TRA) { r = e % TM; k = e / TM; } else { k = e % BK; r = e / BK; }
-        int gi = i0 + r, gk = k0 + k;
-        float v = 0.f;
-        if (gi < tk.M && gk < tm.K)
-          v = TRA ? ldg<TIN>(tm.A, (long long)gk + (long long)gi * tm.lda)
-                  : ldg<TIN>(tm.A, (long long)gi + (long long)gk * tm.lda);
-        float hi = tf32_hi(v);
-        uint32_t o = kmaj_off(r, k);
-        *reinterpret_cast<float*>(sAhi + o) = hi;
-        *reinterpret_cast<float*>(sAlo + o) = v - hi;
+  // flatten (term, k-chunk) pairs
+  int nchunks = 0;
+  for (int t = tk.t0; t < tk.t0 + tk.nt; ++t) nchunks += (terms[t].K + BK - 1) / BK;
+
+  Stage<TM> ra;
+  Stage<TNB> rb;
+  int cur_t = tk.t0, cur_k = 0;
+  GemmTerm tm{};
+  auto load_chunk = [&](int t, int k0) {
+    const GemmTerm g = terms[t];
+    const bool TRA = (g.flags & 1) != 0, TRB = (g.flags & 2) != 0;
+    // op(A)(i, k): TRA -> A[k + i*lda] (contiguous along k)
+    stage_load<TM>(ra, reinterpret_cast<const float*>(g.A), g.lda, TRA, i0, tk.M, k0, g.K);
+    // B operand rows are output columns n: op(B)(k, n) = TRB ? B[n + k*ldb] : B[k + n*ldb]
+    stage_load<TNB>(rb, reinterpret_cast<const float*>(g.B), g.ldb, !TRB, j0, tk.N, k0, g.K);
+  };
+  bool contigA = false, contigB = false;
+  if (nchunks > 0) {
+    // first term with K > 0
+    while (cur_t < tk.t0 + tk.nt && terms[cur_t].K <= 0) ++cur_t;
+    tm = terms[cur_t];
+    contigA = (tm.flags & 1) != 0;
+    contigB = (tm.flags & 2) == 0;
+    load_chunk(cur_t, 0);
+  }
+  uint32_t phase[NSTAGE] = {0u, 0u};
+  for (int c = 0; c < nchunks; ++c) {
+    const int st = c % NSTAGE;
+    unsigned char* sA_hi = base + st * STAGE_BYTES;
+    unsigned char* sA_lo = sA_hi + ABYTES;
+    unsigned char* sB_hi = sA_lo + ABYTES;
+    unsigned char* sB_lo = sB_hi + BBYTES;
+    if (c >= NSTAGE) {
+      // the MMAs of chunk c - NSTAGE read this stage: wait for them (bounded)
+      bool ok = mbar_wait(&mbar[st], phase[st]);
+      phase[st] ^= 1u;
+      if (!ok && tid == 0) {
+        s_fail = 1;
+        atomicExch(err, 1);
       }
-      for (int e = tid; e < TN * BK; e += NTH) {
-        int r, k;
-        if (TRB) { r = e % TN; k = e / TN; } else { k = e % BK; r = e / BK; }
-        int gj = j0 + r, gk = k0 + k;
-        float v = 0.f;
-        if (gj < tk.N && gk < tm.K)
-          v = TRB ? ldg<TIN>(tm.B, (long long)gj + (long long)gk * tm.ldb)
-                  : ldg<TIN>(tm.B, (long long)gk + (long long)gj * tm.ldb);
-        float hi = tf32_hi(v);
-        uint32_t o = kmaj_off(r, k);
-        *reinterpret_cast<float*>(sBhi + o) = hi;
-        *reinterpret_cast<float*>(sBlo + o) = v - hi;
+    }
+    stage_store<TM>(ra, contigA, sA_hi, sA_lo);
+    stage_store<TNB>(rb, contigB, sB_hi, sB_lo);
+    // prefetch the next chunk into registers while the tensor core works
+    {
+      int nt = cur_t, nk = cur_k + BK;
+      if (nk >= terms[cur_t].K) {
+        nt = cur_t + 1;
+        nk = 0;
+        while (nt < tk.t0 + tk.nt && terms[nt].K <= 0) ++nt;
       }
-      // make the generic-proxy smem writes visible to the tensor core
-      asm volatile("fence.proxy.async.shared::cta;");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t aH = smem_u32(sAhi), aL = smem_u32(sAlo), bH = smem_u32(sBhi), bL = smem_u32(sBlo);
+      if (c + 1 < nchunks) {
+        load_chunk(nt, nk);
+        const GemmTerm g = terms[nt];
+        // remember the layouts of the prefetched chunk for its store
+        cur_t = nt;
+        cur_k = nk;
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0 && !s_fail) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t aH = smem_u32(sA_hi), aL = smem_u32(sA_lo), bH = smem_u32(sB_hi), bL = smem_u32(sB_lo);
 #pragma unroll
-        for (int ks = 0; ks < BK / 8; ++ks) {
-          const uint32_t off = ks * 2 * 128;   // K = 8 tf32 = two 16-byte core-matrix columns
-          mma_tf32(tmem, smem_desc(aH + off), smem_desc(bH + off), idesc, first ? 0u : 1u);
-          first = false;
-          mma_tf32(tmem, smem_desc(aH + off), smem_desc(bL + off), idesc, 1u);
-          mma_tf32(tmem, smem_desc(aL + off), smem_desc(bH + off), idesc, 1u);
+          for (int ks = 0; ks < BK / 8; ++ks) {
+            const uint32_t off = ks * 2 * 128;
+            mma_tf32(tmem, smem_desc(aH + off), smem_desc(bH + off), idesc, (c == 0 && ks == 0) ? 0u : 1u);
+            mma_tf32(tmem, smem_desc(aH + off), smem_desc(bL + off), idesc, 1u);
+            mma_tf32(tmem, smem_desc(aL + off), smem_desc(bH + off), idesc, 1u);
+          }
+          mma_commit(&mbar[st]);
         }
-        mma_commit(&mbar);
-      }
-      first = false;
-      __syncthreads();
-      // wait for the MMAs to finish reading shared memory (bounded)
-      bool ok = mbar_wait(&mbar, phase);
-      phase ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (!ok) {
-        if (tid == 0) {
-          s_fail = 1;
-          atomicExch(err, 1);
+        contigA = (g.flags & 1) != 0;
+        contigB = (g.flags & 2) == 0;
+      } else {
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0 && !s_fail) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t aH = smem_u32(sA_hi), aL = smem_u32(sA_lo), bH = smem_u32(sB_hi), bL = smem_u32(sB_lo);
+#pragma unroll
+          for (int ks = 0; ks < BK / 8; ++ks) {
+            const uint32_t off = ks * 2 * 128;
+            mma_tf32(tmem, smem_desc(aH + off), smem_desc(bH + off), idesc, (c == 0 && ks == 0) ? 0u : 1u);
+            mma_tf32(tmem, smem_desc(aH + off), smem_desc(bL + off), idesc, 1u);
+            mma_tf32(tmem, smem_desc(aL + off), smem_desc(bH + off), idesc, 1u);
+          }
+          mma_commit(&mbar[st]);
         }
       }
-      __syncthreads();
-      if (s_fail) break;
     }
   }
+  // wait for the last commit (it completes after every earlier MMA)
+  if (nchunks > 0) {
+    const int st = (nchunks - 1) % NSTAGE;
+    bool ok = mbar_wait(&mbar[st], phase[st]);
+    if (!ok && tid == 0) {
+      s_fail = 1;
+      atomicExch(err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
 
-  // ---- epilogue: TMEM -> registers -> global (warps 0-3 and 4-7 split the columns)
-  if (!s_fail && !first) {
-    const int lane_grp = warp & 3;          // TMEM lanes 32*lane_grp .. +31
-    const int col_half = warp >> 2;         // columns [0,64) or [64,128)
+  float* C = reinterpret_cast<float*>(tk.C);
+  const float* Cin = reinterpret_cast<const float*>(tk.Cin);
+  if (!s_fail && nchunks > 0) {
+    const int lane_grp = warp & 3;             // TMEM lanes 32*lane_grp .. +31
+    const int col_half = warp >> 2;            // columns [0,128) or [128,256)
     const int row = i0 + lane_grp * 32 + lane;
-    float* C = reinterpret_cast<float*>(tk.C);
-    const float* Cin = reinterpret_cast<const float*>(tk.Cin);
 #pragma unroll 1
-    for (int c0 = col_half * 64; c0 < col_half * 64 + 64; c0 += 8) {
+    for (int c0 = col_half * 128; c0 < col_half * 128 + 128; c0 += 8) {
+      if (c0 >= n_mma) break;
       uint32_t r[8];
       uint32_t taddr = tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)c0;
       asm volatile(
@@ -227,11 +311,8 @@ __global__ void __launch_bounds__(NTH, 1) tc_gemm_kernel(const GemmTask* __restr
         }
       }
     }
-  } else if (!s_fail && first) {
-    // task without terms: C = beta * Cin
-    float* C = reinterpret_cast<float*>(tk.C);
-    const float* Cin = reinterpret_cast<const float*>(tk.Cin);
-    for (int e = tid; e < TM * TN; e += NTH) {
+  } else if (!s_fail) {
+    for (int e = tid; e < TM * TNB; e += NTH) {
       int r = i0 + e % TM, c = j0 + e / TM;
       if (r < tk.M && c < tk.N) {
         float v = 0.f;
@@ -243,7 +324,7 @@ __global__ void __launch_bounds__(NTH, 1) tc_gemm_kernel(const GemmTask* __restr
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TNB));
   }
 }
 
@@ -261,11 +342,15 @@ static int* tc_err_flag() {
 void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, int ntasks, int maxM, int maxN,
                     cudaStream_t s) {
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return;
-  const size_t smem = 4 * TILE_BYTES + 1024;
-  H2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(ntasks, ((maxM + TM - 1) / TM) * ((maxN + TN - 1) / TN));
+  const size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
+  static bool attr = false;
+  if (!attr) {
+    H2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  dim3 grid(ntasks, ((maxM + TM - 1) / TM) * ((maxN + TNB - 1) / TNB));
   ProfScope ps("gemm_tc3xtf32", s);
-  tc_gemm_kernel<float><<<grid, NTH, smem, s>>>(d_tasks, d_terms, tc_err_flag());
+  tc_gemm_kernel<<<grid, NTH, smem, s>>>(d_tasks, d_terms, tc_err_flag());
   H2_LAUNCH_CHECK();
 }
 
