@@ -386,6 +386,22 @@ struct Plan {
     o.tag = cur_tag;
     ops.push_back(o);
   }
+  std::vector<long long> gather_n;
+  void gather_rows(const double* src, long long lds, double* dst, long long ldd, const int* idx, long long n,
+                   int nrhs) {
+    Op o{};
+    o.kind = 5;
+    o.x = src;
+    o.y = dst;
+    o.ld = lds;
+    o.tasks = idx;
+    o.n = nrhs;
+    o.a = (int)ldd;
+    gather_n.push_back(n);
+    o.b = (int)(gather_n.size() - 1);
+    o.tag = cur_tag;
+    ops.push_back(o);
+  }
   void gather(const std::vector<GatherTask>& v, const std::vector<long long>& offs, const double* part, double* y,
               long long ldy, int nrhs) {
     Op o{};
@@ -409,6 +425,8 @@ struct Plan {
       else if (o.kind == 3) launch_symv_pairs((const SymPairTask*)o.tasks, o.n, o.x, o.ld, o.y, o.a, st);
       else if (o.kind == 4)
         launch_gather_parts((const GatherTask*)o.tasks, o.n, (const long long*)o.terms, o.x, o.y, o.ld, o.a, st);
+      else if (o.kind == 5)
+        launch_gather_rows(o.x, o.ld, o.y, o.a, (const int*)o.tasks, gather_n[o.b], o.n, st);
     }
     prof_tag(nullptr);
   }
@@ -466,8 +484,12 @@ struct Height {
   std::vector<int> n_op, r_op;
   std::vector<std::vector<int>> cand_op, sk_op;   // global tree-order point ids
   std::vector<DBufP> P_op;           // n_op x r_op interpolation (FP64)
-  std::vector<DBufP> Kfar_op;        // per far pair (flattened in near/far order)
-  std::vector<size_t> far_off;       // prefix of far pairs per box
+  DBufP Kcat_op;                     // per box: [K(sk_I, sk_J1) K(sk_I, sk_J2) ...] (r_I x sum r_J)
+  std::vector<size_t> kcat_off;      // element offsets per box
+  std::vector<int> kcat_cols;        // sum of r_J over the far list
+  DBufP far_gidx;                    // gather index into the skeleton vector, per box concatenated
+  std::vector<size_t> fg_off;        // offsets into far_gidx (= skeleton-gather vector offsets)
+  size_t fg_len = 0;
   std::vector<int64_t> xh_off;       // skeleton-vector offsets
   int64_t xh_len = 0;
   // ULV factor
@@ -482,6 +504,10 @@ struct Height {
   DBufP pivRR;                       // per box m ints (offsets q_off-free: pv_off)
   std::vector<size_t> pv_off;
   DBufP W;                           // per box r x r FP64 (triangular factor of the ID)
+  DBufP Linv, Uinv;                  // per box m x m FP64: L^-1 P^T and U^-1 of the S^RR LU (solve sweeps)
+  std::vector<size_t> li_off;
+  std::vector<int64_t> y_off;        // redundant-part vector offsets (solve)
+  int64_t y_len = 0;
   std::vector<size_t> w_off;
   std::vector<int64_t> v_off;        // level-vector offsets (solve)
   int64_t v_len = 0;
@@ -780,27 +806,46 @@ static void build_operator(Handle& h) {
     }
     run_trsm(Prec::F64, false, false, false, tt, maxrhs, sc);
     run_interp(Prec::F64, it, sc);
-    // far skeleton blocks K(sk_I, sk_J)
-    ht.far_off.assign(ht.nb + 1, 0);
-    for (int g = 0; g < ht.nb; ++g) ht.far_off[g + 1] = ht.far_off[g] + ht.far[g].size();
+    // far skeleton blocks, concatenated per box: K(sk_I, [sk_J for J in far(I)])
     std::vector<int> sk_all;
     std::vector<size_t> sk_off(ht.nb + 1, 0);
     for (int g = 0; g < ht.nb; ++g) {
       sk_all.insert(sk_all.end(), ht.sk_op[g].begin(), ht.sk_op[g].end());
       sk_off[g + 1] = sk_all.size();
     }
+    ht.kcat_off.assign(ht.nb + 1, 0);
+    ht.kcat_cols.assign(ht.nb, 0);
+    ht.fg_off.assign(ht.nb + 1, 0);
+    std::vector<int> colpts;      // far skeleton points, per box concatenated
+    std::vector<int> gidx;        // their positions in the height's skeleton vector
+    std::vector<int64_t> xo(ht.nb + 1, 0);
+    for (int g = 0; g < ht.nb; ++g) xo[g + 1] = xo[g] + ht.r_op[g];
+    for (int g = 0; g < ht.nb; ++g) {
+      int cols = 0;
+      for (int j : ht.far[g]) {
+        colpts.insert(colpts.end(), ht.sk_op[j].begin(), ht.sk_op[j].end());
+        for (int q = 0; q < ht.r_op[j]; ++q) gidx.push_back((int)(xo[j] + q));
+        cols += ht.r_op[j];
+      }
+      ht.kcat_cols[g] = cols;
+      ht.kcat_off[g + 1] = ht.kcat_off[g] + (size_t)ht.r_op[g] * cols;
+      ht.fg_off[g + 1] = ht.fg_off[g] + cols;
+    }
+    ht.fg_len = ht.fg_off[ht.nb];
     int* d_sk = sc.up(sk_all);
-    ht.Kfar_op.resize(ht.far_off[ht.nb]);
+    int* d_cols = sc.up(colpts);
+    ht.Kcat_op = std::make_shared<DBuf>(std::max<size_t>(1, ht.kcat_off[ht.nb]) * 8);
+    ht.far_gidx = std::make_shared<DBuf>(std::max<size_t>(1, gidx.size()) * 4);
+    if (!gidx.empty())
+      H2_CUDA(cudaMemcpy(ht.far_gidx->p, gidx.data(), gidx.size() * 4, cudaMemcpyHostToDevice));
     std::vector<AsmTask> at;
     int maxc = 0;
-    for (int g = 0; g < ht.nb; ++g)
-      for (size_t q = 0; q < ht.far[g].size(); ++q) {
-        int j = ht.far[g][q];
-        auto blk = std::make_shared<DBuf>((size_t)ht.r_op[g] * ht.r_op[j] * 8);
-        ht.Kfar_op[ht.far_off[g] + q] = blk;
-        at.push_back(AsmTask{blk->p, d_sk + sk_off[g], d_sk + sk_off[j], 0, 0, ht.r_op[g], ht.r_op[j], ht.r_op[g]});
-        maxc = std::max(maxc, ht.r_op[j]);
-      }
+    for (int g = 0; g < ht.nb; ++g) {
+      if (ht.kcat_cols[g] == 0) continue;
+      at.push_back(AsmTask{ht.Kcat_op->as<double>() + ht.kcat_off[g], d_sk + sk_off[g], d_cols + ht.fg_off[g], 0, 0,
+                           ht.r_op[g], ht.kcat_cols[g], ht.r_op[g]});
+      maxc = std::max(maxc, ht.kcat_cols[g]);
+    }
     run_assemble(Prec::F64, at, 256, maxc, pts, h.kp, sc);
     // skeleton-vector offsets
     ht.xh_off.assign(ht.nb + 1, 0);
@@ -915,18 +960,21 @@ static PlanP build_matvec_plan(Handle& h, const double* x, double* y, int nrhs) 
     }
     pl.gemm(Prec::F64, gb, true, false);
   }
-  // far interactions at every height (every box gets a task, so the
-  // skeleton vectors are overwritten on each replay)
+  // far interactions at every height: gather the far skeleton values of
+  // each box into one contiguous vector, then one product per box with its
+  // concatenated far block (every box gets a task, so the skeleton vectors
+  // are overwritten on each replay)
   for (int H = 0; H < h.Hmax; ++H) {
     Height& ht = h.hs[H];
+    double* xg = pl.work(std::max<size_t>(1, ht.fg_len) * nrhs);
+    if (ht.fg_len)
+      pl.gather_rows(xh[H], ht.xh_len, xg, (long long)ht.fg_len, ht.far_gidx->as<int>(), (long long)ht.fg_len, nrhs);
     GemmBatch gb;
     for (int g = 0; g < ht.nb; ++g) {
       std::vector<GemmTerm> ts;
-      for (size_t q = 0; q < ht.far[g].size(); ++q) {
-        int j = ht.far[g][q];
-        ts.push_back(GemmTerm{ht.Kfar_op[ht.far_off[g] + q]->p, xh[H] + ht.xh_off[j], ht.r_op[j], ht.r_op[g],
-                              (int)ht.xh_len});
-      }
+      if (ht.kcat_cols[g])
+        ts.push_back(GemmTerm{ht.Kcat_op->as<double>() + ht.kcat_off[g], xg + ht.fg_off[g], ht.kcat_cols[g], ht.r_op[g],
+                              (int)ht.fg_len, 0});
       gb.add(yh[H] + ht.xh_off[g], (int)ht.xh_len, ht.r_op[g], nrhs, 1.0, 0.0, nullptr, 0, ts);
     }
     pl.gemm(Prec::F64, gb, false, false);
@@ -1389,18 +1437,36 @@ static void factor(Handle& h, int precision, int spd) {
         gb.add1(Mm + off[g], n[g], n[g], r[g], Tcur->as<double>() + t_off[g], n[g], P + off[g], n[g], n[g]);
       gb.run(Prec::F64, false, false, sc);
     }
-    // orthogonalise: Q = [U^R U^S], W (r x r)
+    // orthogonalise: Q = [U^R U^S], W (r x r).  In mixed precision the
+    // orthogonalisation runs in FP32 (Q and W only precondition there).
     ht.q_off = off;
     ht.Q = std::make_shared<DBuf>(NN * 8);
     ht.w_off.assign(nb + 1, 0);
     for (int g = 0; g < nb; ++g) ht.w_off[g + 1] = ht.w_off[g] + (size_t)r[g] * r[g];
     ht.W = std::make_shared<DBuf>(std::max<size_t>(1, ht.w_off[nb]) * 8);
-    {
+    if (W == Prec::F64) {
       double* V = (double*)sc.alloc(NN * 8);
       std::vector<HqrTask> qt;
       for (int g = 0; g < nb; ++g)
         qt.push_back(HqrTask{Mm + off[g], V + off[g], ht.Q->as<double>() + off[g], ht.W->as<double>() + ht.w_off[g], n[g], r[g]});
       run_hqr(Prec::F64, qt, sc);
+    } else {
+      float* Mf = (float*)sc.alloc(NN * 4);
+      float* V = (float*)sc.alloc(NN * 4);
+      float* Qf = (float*)sc.alloc(NN * 4);
+      float* Wf = (float*)sc.alloc(std::max<size_t>(1, ht.w_off[nb]) * 4);
+      std::vector<CopyTask> c1, c2, c3;
+      std::vector<HqrTask> qt;
+      for (int g = 0; g < nb; ++g) {
+        c1.push_back(CopyTask{Mm + off[g], Mf + off[g], n[g], r[g], n[g], n[g]});
+        qt.push_back(HqrTask{Mf + off[g], V + off[g], Qf + off[g], Wf + ht.w_off[g], n[g], r[g]});
+        c2.push_back(CopyTask{Qf + off[g], ht.Q->as<double>() + off[g], n[g], n[g], n[g], n[g]});
+        c3.push_back(CopyTask{Wf + ht.w_off[g], ht.W->as<double>() + ht.w_off[g], r[g], r[g], r[g], r[g]});
+      }
+      run_copy(Prec::F64, Prec::F32, false, c1, maxn, maxn, sc);
+      run_hqr(Prec::F32, qt, sc);
+      run_copy(Prec::F32, Prec::F64, false, c2, maxn, maxn, sc);
+      run_copy(Prec::F32, Prec::F64, false, c3, 256, 256, sc);
     }
     const void* Qw = ht.Q->p;
     const void* Ww = ht.W->p;
@@ -1604,6 +1670,25 @@ static void factor(Handle& h, int precision, int spd) {
         }
         gb.run(Prec::F64, true, false, sc);
       }
+      // explicit L^-1 P^T and U^-1 of every S^RR LU: the solve sweeps apply
+      // them as products instead of sequential triangular solves
+      ht.li_off.assign(nb + 1, 0);
+      for (int g = 0; g < nb; ++g) ht.li_off[g + 1] = ht.li_off[g] + (size_t)m[g] * m[g];
+      ht.Linv = std::make_shared<DBuf>(std::max<size_t>(1, ht.li_off[nb]) * 8);
+      ht.Uinv = std::make_shared<DBuf>(std::max<size_t>(1, ht.li_off[nb]) * 8);
+      {
+        std::vector<TrsmTask> tl, tu;
+        for (int g = 0; g < nb; ++g) {
+          if (m[g] == 0) continue;
+          launch_fill_eye(Prec::F64, ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], s);
+          launch_fill_eye(Prec::F64, ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], s);
+          tl.push_back(TrsmTask{S + off[g], ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], n[g], m[g],
+                                ht.pivRR->as<int>() + ht.pv_off[g]});
+          tu.push_back(TrsmTask{S + off[g], ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], n[g], m[g], nullptr});
+        }
+        run_trsm(Prec::F64, true, true, false, tl, maxm, sc);
+        run_trsm(Prec::F64, false, false, false, tu, maxm, sc);
+      }
       // S^SS_II -> parent quadrant
       std::vector<CopyTask> cs;
       for (int g = 0; g < nb; ++g) {
@@ -1644,6 +1729,9 @@ static void factor(Handle& h, int precision, int spd) {
     ht.v_off.assign(nb + 1, 0);
     for (int g = 0; g < nb; ++g) ht.v_off[g + 1] = ht.v_off[g] + n[g];
     ht.v_len = ht.v_off[nb];
+    ht.y_off.assign(nb + 1, 0);
+    for (int g = 0; g < nb; ++g) ht.y_off[g + 1] = ht.y_off[g] + m[g];
+    ht.y_len = ht.y_off[nb];
     H2_CUDA(cudaStreamSynchronize(s));
     h.level_ms.push_back(now_ms() - t0);
   }
@@ -1671,10 +1759,11 @@ static PlanP build_ulv_plan(Handle& h, const double* b, double* x, int nrhs) {
   auto P = std::make_shared<Plan>();
   Plan& pl = *P;
   const int64_t ld = h.Ntot;
-  std::vector<double*> c(h.Hmax), xo(h.Hmax);
+  std::vector<double*> c(h.Hmax), xo(h.Hmax), yb(h.Hmax);
   for (int H = 0; H < h.Hmax; ++H) {
     c[H] = pl.work((size_t)h.hs[H].v_len * nrhs);
     xo[H] = pl.work((size_t)h.hs[H].v_len * nrhs);
+    yb[H] = pl.work((size_t)std::max<int64_t>(1, h.hs[H].y_len) * nrhs);
   }
   std::vector<double*> rootb(h.probs.size(), nullptr), rootx(h.probs.size(), nullptr);
   for (size_t p = 0; p < h.probs.size(); ++p)
@@ -1713,17 +1802,18 @@ static PlanP build_ulv_plan(Handle& h, const double* b, double* x, int nrhs) {
               ht.n[g]);
     }
     pl.gemm(Prec::F64, g1, true, false);
-    std::vector<TrsmTask> tl;
-    GemmBatch g2;
+    // y_R = (L^-1 P^T) c_R, then c_S -= L^SR y_R
+    const int64_t ly = std::max<int64_t>(1, ht.y_len);
+    GemmBatch gl, g2;
     for (int g = 0; g < nb; ++g) {
       int m = ht.n[g] - ht.r[g];
       if (m == 0) continue;
-      double* Sg = ht.S->as<double>() + ht.q_off[g];
-      tl.push_back(TrsmTask{Sg, c[H] + ht.v_off[g], m, nrhs, ht.n[g], (int)lv, ht.pivRR->as<int>() + ht.pv_off[g]});
+      gl.add1(yb[H] + ht.y_off[g], (int)ly, m, nrhs, ht.Linv->as<double>() + ht.li_off[g], m, c[H] + ht.v_off[g],
+              (int)lv, m);
       g2.add1(c[H] + ht.v_off[g] + m, (int)lv, ht.r[g], nrhs, ht.Lt->as<double>() + ht.lt_off[g], m,
-              c[H] + ht.v_off[g], (int)lv, m, -1.0, 1.0);
+              yb[H] + ht.y_off[g], (int)ly, m, -1.0, 1.0);
     }
-    pl.trsm(Prec::F64, true, true, false, tl, nrhs);
+    pl.gemm(Prec::F64, gl, false, false);
     pl.gemm(Prec::F64, g2, true, false);
     // gather skeleton parts into the next height's input (stored in xo[H])
     std::vector<CopyTask> ct;
@@ -1787,18 +1877,20 @@ static PlanP build_ulv_plan(Handle& h, const double* b, double* x, int nrhs) {
       ct.push_back(CopyTask{src, c[H] + ht.v_off[g] + m, ht.r[g], nrhs, lds, (int)lv});
     }
     pl.copy(Prec::F64, Prec::F64, false, ct, 256, nrhs);
-    GemmBatch g1;
-    std::vector<TrsmTask> tu;
+    // x_R = U^-1 (y_R - U^RS x_S)
+    const int64_t ly = std::max<int64_t>(1, ht.y_len);
+    GemmBatch g1, gu;
     for (int g = 0; g < nb; ++g) {
       int m = ht.n[g] - ht.r[g];
       if (m == 0) continue;
       double* Sg = ht.S->as<double>() + ht.q_off[g];
-      g1.add1(c[H] + ht.v_off[g], (int)lv, m, nrhs, Sg + (size_t)m * ht.n[g], ht.n[g], c[H] + ht.v_off[g] + m, (int)lv,
+      g1.add1(yb[H] + ht.y_off[g], (int)ly, m, nrhs, Sg + (size_t)m * ht.n[g], ht.n[g], c[H] + ht.v_off[g] + m, (int)lv,
               ht.r[g], -1.0, 1.0);
-      tu.push_back(TrsmTask{Sg, c[H] + ht.v_off[g], m, nrhs, ht.n[g], (int)lv, nullptr});
+      gu.add1(c[H] + ht.v_off[g], (int)lv, m, nrhs, ht.Uinv->as<double>() + ht.li_off[g], m, yb[H] + ht.y_off[g],
+              (int)ly, m);
     }
     pl.gemm(Prec::F64, g1, false, false);
-    pl.trsm(Prec::F64, false, false, false, tu, nrhs);
+    pl.gemm(Prec::F64, gu, false, false);
     GemmBatch g2;
     for (int g = 0; g < nb; ++g) {
       double* dst;

@@ -214,6 +214,8 @@ void launch_axpy_cols(double* Y, const double* X, int n, int nrhs, int64_t ldy, 
                       double alpha, cudaStream_t s);
 void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int64_t* map,
                          int64_t n, int nrhs, bool scatter, cudaStream_t s);
+void launch_gather_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int* idx, int64_t n, int nrhs,
+                        cudaStream_t s);
 void launch_fill_eye(Prec p, void* A, int n, int ld, cudaStream_t s);
 void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int k0, int k1,
                        int col_begin, int col_end, cudaStream_t s);

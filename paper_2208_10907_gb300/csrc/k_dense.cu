@@ -119,12 +119,11 @@ __global__ void __launch_bounds__(NT) getrf_kernel(const LuTask* __restrict__ ta
     }
     for (int j = k + 1 + threadIdx.x; j < nc; j += NT) rowk[j] = A[k + (long long)j * lda];
     __syncthreads();
-    const int rows = m - k - 1, cols = nc - k - 1;
-    const long long cnt = (long long)rows * cols;
-    for (long long e = threadIdx.x; e < cnt; e += NT) {
-      int i = k + 1 + (int)(e % rows);
-      int j = k + 1 + (int)(e / rows);
-      A[i + (long long)j * lda] -= colk[i] * rowk[j];
+    // trailing update, column by column, rows spread over the threads
+    for (int j = k + 1; j < nc; ++j) {
+      const T rj = rowk[j];
+      T* col = A + (long long)j * lda;
+      for (int i = k + 1 + threadIdx.x; i < m; i += NT) col[i] -= colk[i] * rj;
     }
     __syncthreads();
   }
@@ -712,6 +711,16 @@ __global__ void permute_rows_kernel(const double* src, long long lds, double* ds
   }
 }
 
+__global__ void gather_rows_kernel(const double* src, long long lds, double* dst, long long ldd, const int* idx,
+                                   long long n, int nrhs) {
+  long long cnt = n * nrhs;
+  for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < cnt; e += (long long)gridDim.x * NT) {
+    long long i = e % n;
+    int c = (int)(e / n);
+    dst[i + c * ldd] = src[idx[i] + c * lds];
+  }
+}
+
 template <typename T> __global__ void eye_kernel(T* A, int n, int ld) {
   long long cnt = (long long)n * n;
   for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < cnt; e += (long long)gridDim.x * NT) {
@@ -913,6 +922,16 @@ void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ld
   ProfScope ps("permute", s);
   int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
   permute_rows_kernel<<<g, NT, 0, s>>>(src, lds, dst, ldd, map, n, nrhs, scatter);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_gather_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int* idx, int64_t n, int nrhs,
+                        cudaStream_t s) {
+  long long cnt = (long long)n * nrhs;
+  if (cnt <= 0) return;
+  ProfScope ps("gather_rows", s);
+  int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
+  gather_rows_kernel<<<g, NT, 0, s>>>(src, lds, dst, ldd, idx, n, nrhs);
   H2_LAUNCH_CHECK();
 }
 
