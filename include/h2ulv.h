@@ -128,8 +128,11 @@ h2_status h2_factor(h2_handle h, int32_t precision, int32_t spd);
 
 /* Solve A x = b with the ULV factors (Sec. II-B: L z = U^T b, U y = z,
  * x = V^T y) and FP64 iterative refinement whose residual is the H^2
- * matvec: x <- x + ULV^-1 (b - A_H2 x) until ||r|| / ||b|| <= target for
- * every right-hand side or max_iter corrections were applied.
+ * matvec, until ||b - A_H2 x|| / ||b|| <= target for every right-hand side
+ * or max_iter corrections were applied.  With nrhs <= 8 the correction
+ * equation is solved by GMRES(30) preconditioned by the ULV factors (each
+ * Arnoldi step = one ULV solve + one H^2 matvec, counted as one
+ * correction); otherwise x <- x + ULV^-1 (b - A_H2 x).
  *   b, x   : N x nrhs column-major, leading dimension ld (host or device)
  *   achieved_rel_residual : host array of nrhs (may be NULL)
  *   iters  : host int, corrections applied (may be NULL)

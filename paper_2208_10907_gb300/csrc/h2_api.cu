@@ -556,6 +556,9 @@ struct Handle {
   struct SolvePlans {
     int nrhs = 0;
     double *B = nullptr, *X = nullptr, *R = nullptr, *Uin = nullptr, *Uout = nullptr, *nrm = nullptr;
+    // GMRES workspace (allocated on first use)
+    double *V = nullptr, *Xsol = nullptr, *hdev = nullptr, *part = nullptr, *ydev = nullptr;
+    int m = 0;
     PlanP ulv, mv;
     std::vector<DBufP> bufs;
   };
@@ -842,9 +845,11 @@ static void build_operator(Handle& h) {
     int maxc = 0;
     for (int g = 0; g < ht.nb; ++g) {
       if (ht.kcat_cols[g] == 0) continue;
-      at.push_back(AsmTask{ht.Kcat_op->as<double>() + ht.kcat_off[g], d_sk + sk_off[g], d_cols + ht.fg_off[g], 0, 0,
-                           ht.r_op[g], ht.kcat_cols[g], ht.r_op[g]});
-      maxc = std::max(maxc, ht.kcat_cols[g]);
+      // stored transposed: K(far skeletons, sk_I), so each output row of the
+      // far product is a contiguous column (warp dot products in the matvec)
+      at.push_back(AsmTask{ht.Kcat_op->as<double>() + ht.kcat_off[g], d_cols + ht.fg_off[g], d_sk + sk_off[g], 0, 0,
+                           ht.kcat_cols[g], ht.r_op[g], ht.kcat_cols[g]});
+      maxc = std::max(maxc, ht.r_op[g]);
     }
     run_assemble(Prec::F64, at, 256, maxc, pts, h.kp, sc);
     // skeleton-vector offsets
@@ -973,8 +978,8 @@ static PlanP build_matvec_plan(Handle& h, const double* x, double* y, int nrhs) 
     for (int g = 0; g < ht.nb; ++g) {
       std::vector<GemmTerm> ts;
       if (ht.kcat_cols[g])
-        ts.push_back(GemmTerm{ht.Kcat_op->as<double>() + ht.kcat_off[g], xg + ht.fg_off[g], ht.kcat_cols[g], ht.r_op[g],
-                              (int)ht.fg_len, 0});
+        ts.push_back(GemmTerm{ht.Kcat_op->as<double>() + ht.kcat_off[g], xg + ht.fg_off[g], ht.kcat_cols[g],
+                              ht.kcat_cols[g], (int)ht.fg_len, 1});
       gb.add(yh[H] + ht.xh_off[g], (int)ht.xh_len, ht.r_op[g], nrhs, 1.0, 0.0, nullptr, 0, ts);
     }
     pl.gemm(Prec::F64, gb, false, false);
@@ -1677,11 +1682,18 @@ static void factor(Handle& h, int precision, int spd) {
       ht.Linv = std::make_shared<DBuf>(std::max<size_t>(1, ht.li_off[nb]) * 8);
       ht.Uinv = std::make_shared<DBuf>(std::max<size_t>(1, ht.li_off[nb]) * 8);
       {
+        double* I256 = (double*)sc.alloc(256 * 256 * 8);
+        launch_fill_eye(Prec::F64, I256, 256, 256, s);
+        std::vector<CopyTask> ci;
+        for (int g = 0; g < nb; ++g) {
+          if (m[g] == 0) continue;
+          ci.push_back(CopyTask{I256, ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], 256, m[g]});
+          ci.push_back(CopyTask{I256, ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], 256, m[g]});
+        }
+        run_copy(Prec::F64, Prec::F64, false, ci, 256, 256, sc);
         std::vector<TrsmTask> tl, tu;
         for (int g = 0; g < nb; ++g) {
           if (m[g] == 0) continue;
-          launch_fill_eye(Prec::F64, ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], s);
-          launch_fill_eye(Prec::F64, ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], s);
           tl.push_back(TrsmTask{S + off[g], ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], n[g], m[g],
                                 ht.pivRR->as<int>() + ht.pv_off[g]});
           tu.push_back(TrsmTask{S + off[g], ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], n[g], m[g], nullptr});
@@ -2129,6 +2141,138 @@ static void from_tree(Handle& h, const double* src_tree, double* dst, int64_t ld
   H2_CUDA(cudaStreamSynchronize(h.s));
 }
 
+
+// GMRES-based refinement (right preconditioned): FP64 GMRES(m) on the H^2
+// operator, ULV factors as the preconditioner, classical Gram-Schmidt applied
+// twice, everything on the device except the small Givens / least-squares
+// work on the Hessenberg columns (one device-to-host read per Arnoldi step).
+static void gmres_solve(Handle& h, Handle::SolvePlans& sp, int nrhs, double target, int max_iter,
+                        const std::vector<double>& bn2, std::vector<double>& rel, int& iters, bool& converged) {
+  const int64_t N = h.Ntot;
+  const size_t blk = (size_t)N * nrhs;
+  const int m = std::max(1, std::min(30, max_iter));
+  if (!sp.V || sp.m < m) {
+    auto mk = [&](size_t e) {
+      auto b = std::make_shared<DBuf>(std::max<size_t>(e, 2) * 8);
+      sp.bufs.push_back(b);
+      return b->as<double>();
+    };
+    sp.V = mk(blk * (m + 1));
+    sp.Xsol = mk(blk);
+    sp.hdev = mk((size_t)nrhs * 3 * 32);
+    sp.part = mk((size_t)608 * 32);
+    sp.ydev = mk((size_t)nrhs * 32);
+    sp.m = m;
+  }
+  cudaStream_t s = h.s;
+  std::vector<double> bnorm(nrhs);
+  for (int c = 0; c < nrhs; ++c) bnorm[c] = bn2[c] > 0 ? std::sqrt(bn2[c]) : 1.0;
+  // x0 = ULV^-1 b
+  H2_CUDA(cudaMemcpyAsync(sp.Uin, sp.B, blk * 8, cudaMemcpyDeviceToDevice, s));
+  sp.ulv->run(s);
+  H2_CUDA(cudaMemcpyAsync(sp.Xsol, sp.Uout, blk * 8, cudaMemcpyDeviceToDevice, s));
+  iters = 0;
+  converged = false;
+  std::vector<double> rn(nrhs), hh((size_t)nrhs * 3 * 32), nrm2(nrhs);
+  Scratch sc(s);
+  while (true) {
+    // R = A x - b, the FP64 H^2 residual
+    H2_CUDA(cudaMemcpyAsync(sp.X, sp.Xsol, blk * 8, cudaMemcpyDeviceToDevice, s));
+    sp.mv->run(s);
+    launch_axpy_cols(sp.R, sp.B, (int)N, nrhs, N, N, -1.0, s);
+    launch_colnorm2(sp.R, (int)N, nrhs, N, sp.nrm, s);
+    H2_CUDA(cudaMemcpyAsync(rn.data(), sp.nrm, nrhs * 8, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    bool ok = true;
+    for (int c = 0; c < nrhs; ++c) {
+      rel[c] = std::sqrt(rn[c]) / bnorm[c];
+      if (!(rel[c] <= target)) ok = false;
+    }
+    if (ok) {
+      converged = true;
+      return;
+    }
+    if (iters >= max_iter) return;
+    // V_0 = R / ||R||, g = -||R|| e_1
+    for (int c = 0; c < nrhs; ++c)
+      launch_normalize(sp.V + (size_t)c * N, sp.R + (size_t)c * N, N, sp.nrm + c, s);
+    std::vector<std::vector<double>> H((size_t)nrhs, std::vector<double>((size_t)(m + 1) * m, 0.0));
+    std::vector<std::vector<double>> g((size_t)nrhs, std::vector<double>(m + 1, 0.0));
+    std::vector<std::vector<double>> cs((size_t)nrhs, std::vector<double>(m, 0.0)), sn = cs;
+    for (int c = 0; c < nrhs; ++c) g[c][0] = -std::sqrt(rn[c]);
+    int jend = -1;
+    for (int j = 0; j < m && iters < max_iter; ++j) {
+      double* Vj = sp.V + (size_t)j * blk;
+      H2_CUDA(cudaMemcpyAsync(sp.Uin, Vj, blk * 8, cudaMemcpyDeviceToDevice, s));
+      sp.ulv->run(s);                                                     // Z = M^-1 v_j
+      H2_CUDA(cudaMemcpyAsync(sp.X, sp.Uout, blk * 8, cudaMemcpyDeviceToDevice, s));
+      sp.mv->run(s);                                                      // w = A Z
+      ++iters;
+      for (int c = 0; c < nrhs; ++c) {
+        double* w = sp.R + (size_t)c * N;
+        const double* Vc = sp.V + (size_t)c * N;
+        for (int pass = 0; pass < 2; ++pass) {
+          double* hc = sp.hdev + ((size_t)c * 3 + pass) * 32;
+          launch_mdot(Vc, (int64_t)blk, j + 1, w, N, sp.part, hc, s);
+          GemmBatch gb;
+          gb.add1(w, (int)N, (int)N, 1, Vc, (int)blk, hc, j + 1, j + 1, -1.0, 1.0);
+          gb.run(Prec::F64, false, false, sc);
+        }
+      }
+      launch_colnorm2(sp.R, (int)N, nrhs, N, sp.nrm, s);
+      for (int c = 0; c < nrhs; ++c)
+        launch_normalize(sp.V + (size_t)(j + 1) * blk + (size_t)c * N, sp.R + (size_t)c * N, N, sp.nrm + c, s);
+      H2_CUDA(cudaMemcpyAsync(hh.data(), sp.hdev, hh.size() * 8, cudaMemcpyDeviceToHost, s));
+      H2_CUDA(cudaMemcpyAsync(nrm2.data(), sp.nrm, nrhs * 8, cudaMemcpyDeviceToHost, s));
+      H2_CUDA(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int c = 0; c < nrhs; ++c) {
+        std::vector<double>& Hc = H[c];
+        auto Hx = [&](int i, int jj) -> double& { return Hc[(size_t)i + (size_t)jj * (m + 1)]; };
+        for (int i = 0; i <= j; ++i) Hx(i, j) = hh[((size_t)c * 3 + 0) * 32 + i] + hh[((size_t)c * 3 + 1) * 32 + i];
+        Hx(j + 1, j) = std::sqrt(std::max(0.0, nrm2[c]));
+        for (int i = 0; i < j; ++i) {   // previous rotations
+          double t = cs[c][i] * Hx(i, j) + sn[c][i] * Hx(i + 1, j);
+          Hx(i + 1, j) = -sn[c][i] * Hx(i, j) + cs[c][i] * Hx(i + 1, j);
+          Hx(i, j) = t;
+        }
+        double a0 = Hx(j, j), b0 = Hx(j + 1, j);
+        double rr = std::hypot(a0, b0);
+        cs[c][j] = rr > 0 ? a0 / rr : 1.0;
+        sn[c][j] = rr > 0 ? b0 / rr : 0.0;
+        Hx(j, j) = rr;
+        Hx(j + 1, j) = 0.0;
+        g[c][j + 1] = -sn[c][j] * g[c][j];
+        g[c][j] = cs[c][j] * g[c][j];
+        if (!(std::fabs(g[c][j + 1]) / bnorm[c] <= 0.5 * target)) all = false;
+      }
+      jend = j;
+      if (all) break;
+    }
+    if (jend < 0) return;
+    // x += M^-1 (V y), y = H^-1 g (upper triangular)
+    std::vector<double> y((size_t)nrhs * 32, 0.0);
+    for (int c = 0; c < nrhs; ++c) {
+      auto Hx = [&](int i, int jj) -> double { return H[c][(size_t)i + (size_t)jj * (m + 1)]; };
+      for (int i = jend; i >= 0; --i) {
+        double t = g[c][i];
+        for (int k = i + 1; k <= jend; ++k) t -= Hx(i, k) * y[(size_t)c * 32 + k];
+        y[(size_t)c * 32 + i] = Hx(i, i) != 0.0 ? t / Hx(i, i) : 0.0;
+      }
+    }
+    H2_CUDA(cudaMemcpyAsync(sp.ydev, y.data(), y.size() * 8, cudaMemcpyHostToDevice, s));
+    {
+      GemmBatch gb;
+      for (int c = 0; c < nrhs; ++c)
+        gb.add1(sp.Uin + (size_t)c * N, (int)N, (int)N, 1, sp.V + (size_t)c * N, (int)blk, sp.ydev + (size_t)c * 32,
+                jend + 1, jend + 1);
+      gb.run(Prec::F64, false, false, sc);
+    }
+    sp.ulv->run(s);
+    launch_axpy_cols(sp.Xsol, sp.Uout, (int)N, nrhs, N, N, 1.0, s);
+  }
+}
+
 h2_status h2_matvec(h2_handle H, const double* x, double* y, int32_t nrhs, int64_t ld) {
   if (!H || !x || !y || nrhs < 1 || ld < H->h.Ntot) {
     g_err = "invalid matvec arguments";
@@ -2166,12 +2310,25 @@ h2_status h2_solve(h2_handle H, const double* b, double* x, int32_t nrhs, int64_
     H2_CUDA(cudaStreamSynchronize(h.s));
     for (double v : bn)
       if (!std::isfinite(v)) throw StatusError(H2_ERR_NONFINITE, "non-finite right-hand side");
-    // x0 = ULV^-1 b
+    std::vector<double> rel(nrhs, 0.0);
+    const char* mode = getenv("H2_REFINE");
+    const bool use_gmres = nrhs <= 8 && !(mode && std::string(mode) == "stationary");
+    if (use_gmres) {
+      int it = 0;
+      bool conv = false;
+      gmres_solve(h, sp, nrhs, target, max_iter, bn, rel, it, conv);
+      converged = conv;
+      from_tree(h, sp.Xsol, x, ld, nrhs, sp.Uin);
+      if (achieved)
+        for (int c = 0; c < nrhs; ++c) achieved[c] = rel[c];
+      if (iters) *iters = it;
+      return;
+    }
+    // stationary refinement: x0 = ULV^-1 b, x <- x - ULV^-1 (A x - b)
     H2_CUDA(cudaMemcpyAsync(sp.Uin, sp.B, bytes, cudaMemcpyDeviceToDevice, h.s));
     sp.ulv->run(h.s);
     H2_CUDA(cudaMemcpyAsync(sp.X, sp.Uout, bytes, cudaMemcpyDeviceToDevice, h.s));
     int it = 0;
-    std::vector<double> rel(nrhs, 0.0);
     while (true) {
       sp.mv->run(h.s);                                               // R = A_H2 X
       launch_axpy_cols(sp.R, sp.B, (int)N, nrhs, N, N, -1.0, h.s);   // R = A X - b

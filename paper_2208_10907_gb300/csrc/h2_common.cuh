@@ -214,6 +214,10 @@ void launch_axpy_cols(double* Y, const double* X, int n, int nrhs, int64_t ldy, 
                       double alpha, cudaStream_t s);
 void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int64_t* map,
                          int64_t n, int nrhs, bool scatter, cudaStream_t s);
+// out[i] = <V_i, w> for i < kvec <= 32 (V_i = V + i*ldv); partial needs 608*32 doubles
+void launch_mdot(const double* V, int64_t ldv, int kvec, const double* w, int64_t n, double* partial, double* out,
+                 cudaStream_t s);
+void launch_normalize(double* v, const double* w, int64_t n, const double* norm2, cudaStream_t s);
 void launch_gather_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int* idx, int64_t n, int nrhs,
                         cudaStream_t s);
 void launch_fill_eye(Prec p, void* A, int n, int ld, cudaStream_t s);

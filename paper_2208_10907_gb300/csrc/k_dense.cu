@@ -711,6 +711,43 @@ __global__ void permute_rows_kernel(const double* src, long long lds, double* ds
   }
 }
 
+// out[i] = sum_n V[n + i*ldv] * w[n], i < k <= 32: per-block partials, then
+// a fixed-order reduction over blocks (deterministic).
+constexpr int MDOT_MAXK = 32;
+__global__ void __launch_bounds__(NT) mdot_partial_kernel(const double* __restrict__ V, long long ldv, int k,
+                                                          const double* __restrict__ w, long long n,
+                                                          double* __restrict__ partial) {
+  __shared__ double s[32];
+  double acc[MDOT_MAXK];
+#pragma unroll
+  for (int i = 0; i < MDOT_MAXK; ++i) acc[i] = 0.0;
+  for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < n; e += (long long)gridDim.x * NT) {
+    const double wv = w[e];
+#pragma unroll
+    for (int i = 0; i < MDOT_MAXK; ++i)
+      if (i < k) acc[i] = fma(V[e + i * ldv], wv, acc[i]);
+  }
+#pragma unroll 1
+  for (int i = 0; i < k; ++i) {
+    double t = block_sum(acc[i], s);
+    if (threadIdx.x == 0) partial[(long long)blockIdx.x * MDOT_MAXK + i] = t;
+  }
+}
+
+__global__ void mdot_reduce_kernel(const double* __restrict__ partial, int nblk, int k, double* __restrict__ out) {
+  int i = threadIdx.x;
+  if (i >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(long long)b * MDOT_MAXK + i];
+  out[i] = s;
+}
+
+// v = w / sqrt(norm2[0])
+__global__ void normalize_kernel(double* v, const double* w, long long n, const double* norm2) {
+  const double inv = 1.0 / sqrt(norm2[0]);
+  for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < n; e += (long long)gridDim.x * NT) v[e] = w[e] * inv;
+}
+
 __global__ void gather_rows_kernel(const double* src, long long lds, double* dst, long long ldd, const int* idx,
                                    long long n, int nrhs) {
   long long cnt = n * nrhs;
@@ -922,6 +959,24 @@ void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ld
   ProfScope ps("permute", s);
   int g = (int)std::min<long long>(152 * 8, (cnt + NT - 1) / NT);
   permute_rows_kernel<<<g, NT, 0, s>>>(src, lds, dst, ldd, map, n, nrhs, scatter);
+  H2_LAUNCH_CHECK();
+}
+
+constexpr int MDOT_BLOCKS = 152 * 4;
+void launch_mdot(const double* V, int64_t ldv, int kvec, const double* w, int64_t n, double* partial, double* out,
+                 cudaStream_t s) {
+  if (kvec <= 0) return;
+  if (kvec > MDOT_MAXK) throw StatusError(1, "mdot: more than 32 vectors");
+  ProfScope ps("mdot_f64", s);
+  mdot_partial_kernel<<<MDOT_BLOCKS, NT, 0, s>>>(V, ldv, kvec, w, n, partial);
+  mdot_reduce_kernel<<<1, 32, 0, s>>>(partial, MDOT_BLOCKS, kvec, out);
+  H2_LAUNCH_CHECK();
+}
+
+void launch_normalize(double* v, const double* w, int64_t n, const double* norm2, cudaStream_t s) {
+  ProfScope ps("normalize", s);
+  int g = (int)std::min<long long>(152 * 8, (n + NT - 1) / NT);
+  normalize_kernel<<<g, NT, 0, s>>>(v, w, n, norm2);
   H2_LAUNCH_CHECK();
 }
 
