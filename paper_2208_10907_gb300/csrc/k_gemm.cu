@@ -123,82 +123,113 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmTask* __restrict__ t
 // column.  Transposed terms: one warp per row, lanes along the contiguous
 // column, then a warp reduction.  This is bandwidth-bound by design.
 // ---------------------------------------------------------------------------
-constexpr int GV_ROWS = 256, GV_K = 256, GV_MAXN = 8;
+constexpr int GV_ROWS = 256, GV_MAXN = 8;
 
-template <typename T>
+template <typename T, int NR>
+__device__ __forceinline__ void xload(T (&xv)[GV_MAXN], const T* B, long long k, long long ldb, bool trb, int n) {
+#pragma unroll
+  for (int c = 0; c < GV_MAXN; ++c)
+    if (c < NR) xv[c] = (c < n) ? (trb ? B[c + k * ldb] : B[k + c * ldb]) : (T)0;
+}
+
+template <typename T, int NR>
 __global__ void __launch_bounds__(NT) gemv_kernel(const GemmTask* __restrict__ tasks,
                                                   const GemmTerm* __restrict__ terms) {
   const GemmTask tk = tasks[blockIdx.x];
   const int i0 = blockIdx.y * GV_ROWS;
   if (i0 >= tk.M) return;
   const int rows = min(GV_ROWS, tk.M - i0);
-  const int N = tk.N;
-  __shared__ T xs[GV_K][GV_MAXN];
   __shared__ T yacc[GV_ROWS][GV_MAXN + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < GV_ROWS * (GV_MAXN + 1); e += NT) (&yacc[0][0])[e] = (T)0;
+  bool any_tra = false;
+  for (int t = tk.t0; t < tk.t0 + tk.nt; ++t) any_tra |= (terms[t].flags & 1) != 0;
+  if (any_tra) {
+    for (int e = tid; e < GV_ROWS * (GV_MAXN + 1); e += NT) (&yacc[0][0])[e] = (T)0;
+    __syncthreads();
+  }
+  T racc[GV_MAXN];
+#pragma unroll
+  for (int c = 0; c < GV_MAXN; ++c) racc[c] = (T)0;
   for (int t = tk.t0; t < tk.t0 + tk.nt; ++t) {
     const GemmTerm tm = terms[t];
     const bool TRA = (tm.flags & 1) != 0, TRB = (tm.flags & 2) != 0;
     const T* A = reinterpret_cast<const T*>(tm.A);
     const T* B = reinterpret_cast<const T*>(tm.B);
-    for (int k0 = 0; k0 < tm.K; k0 += GV_K) {
-      const int kc = min(GV_K, tm.K - k0);
-      __syncthreads();
-      for (int e = tid; e < kc * N; e += NT) {
-        int k = e % kc, c = e / kc;
-        xs[k][c] = TRB ? B[c + (long long)(k0 + k) * tm.ldb] : B[(k0 + k) + (long long)c * tm.ldb];
-      }
-      __syncthreads();
-      if (!TRA) {
-        if (tid < rows) {
-          T acc[GV_MAXN];
-#pragma unroll
-          for (int c = 0; c < GV_MAXN; ++c) acc[c] = (T)0;
-          const T* a = A + (i0 + tid) + (long long)k0 * tm.lda;
-#pragma unroll 4
-          for (int k = 0; k < kc; ++k) {
-            T v = a[(long long)k * tm.lda];
-#pragma unroll
-            for (int c = 0; c < GV_MAXN; ++c)
-              if (c < N) acc[c] = fma(v, xs[k][c], acc[c]);
-          }
+    if (!TRA) {
+      // one thread per row; x(k, :) is the same address for every thread
+      if (tid < rows) {
+        const T* a = A + (i0 + tid);
+        int k = 0;
+        for (; k + 4 <= tm.K; k += 4) {
+          T v0 = a[(long long)(k + 0) * tm.lda], v1 = a[(long long)(k + 1) * tm.lda];
+          T v2 = a[(long long)(k + 2) * tm.lda], v3 = a[(long long)(k + 3) * tm.lda];
+          T x0[GV_MAXN], x1[GV_MAXN], x2[GV_MAXN], x3[GV_MAXN];
+          xload<T, NR>(x0, B, k + 0, tm.ldb, TRB, tk.N);
+          xload<T, NR>(x1, B, k + 1, tm.ldb, TRB, tk.N);
+          xload<T, NR>(x2, B, k + 2, tm.ldb, TRB, tk.N);
+          xload<T, NR>(x3, B, k + 3, tm.ldb, TRB, tk.N);
 #pragma unroll
           for (int c = 0; c < GV_MAXN; ++c)
-            if (c < N) yacc[tid][c] += acc[c];
+            if (c < NR) racc[c] = fma(v3, x3[c], fma(v2, x2[c], fma(v1, x1[c], fma(v0, x0[c], racc[c]))));
         }
-      } else {
-        for (int r = warp; r < rows; r += NT / 32) {
-          T acc[GV_MAXN];
+        for (; k < tm.K; ++k) {
+          T v = a[(long long)k * tm.lda];
+          T x0[GV_MAXN];
+          xload<T, NR>(x0, B, k, tm.ldb, TRB, tk.N);
 #pragma unroll
-          for (int c = 0; c < GV_MAXN; ++c) acc[c] = (T)0;
-          const T* a = A + k0 + (long long)(i0 + r) * tm.lda;
-          for (int k = lane; k < kc; k += 32) {
-            T v = a[k];
+          for (int c = 0; c < GV_MAXN; ++c)
+            if (c < NR) racc[c] = fma(v, x0[c], racc[c]);
+        }
+      }
+    } else {
+      // one warp per row: lanes along the contiguous column of the stored matrix
+      for (int r = warp; r < rows; r += NT / 32) {
+        const T* a = A + (long long)(i0 + r) * tm.lda;
+        T acc[GV_MAXN];
 #pragma unroll
-            for (int c = 0; c < GV_MAXN; ++c)
-              if (c < N) acc[c] = fma(v, xs[k][c], acc[c]);
-          }
+        for (int c = 0; c < GV_MAXN; ++c) acc[c] = (T)0;
+        for (int k = lane; k < tm.K; k += 32) {
+          T v = a[k];
+          T x0[GV_MAXN];
+          xload<T, NR>(x0, B, k, tm.ldb, TRB, tk.N);
 #pragma unroll
-          for (int c = 0; c < GV_MAXN; ++c) {
+          for (int c = 0; c < GV_MAXN; ++c)
+            if (c < NR) acc[c] = fma(v, x0[c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < GV_MAXN; ++c) {
+          if (c < NR) {
             T v = acc[c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0 && c < N) yacc[r][c] += v;
+            if (lane == 0) yacc[r][c] += v;
           }
         }
       }
     }
   }
-  __syncthreads();
+  if (any_tra) __syncthreads();
   T* C = reinterpret_cast<T*>(tk.C);
   const T* Cin = reinterpret_cast<const T*>(tk.Cin);
-  for (int e = tid; e < rows * N; e += NT) {
-    int i = e % rows, c = e / rows;
-    T v = (T)tk.alpha * yacc[i][c];
-    if (Cin != nullptr && tk.beta != 0.0) v += (T)tk.beta * Cin[(i0 + i) + (long long)c * tk.ldcin];
-    C[(i0 + i) + (long long)c * tk.ldc] = v;
+  if (tid < rows) {
+#pragma unroll
+    for (int c = 0; c < GV_MAXN; ++c) {
+      if (c < NR && c < tk.N) {
+        T y = racc[c] + (any_tra ? yacc[tid][c] : (T)0);
+        T v = (T)tk.alpha * y;
+        if (Cin != nullptr && tk.beta != 0.0) v += (T)tk.beta * Cin[(i0 + tid) + (long long)c * tk.ldcin];
+        C[(i0 + tid) + (long long)c * tk.ldc] = v;
+      }
+    }
   }
+}
+
+template <typename T>
+void gemv_dispatch(int N, dim3 g, const GemmTask* d_tasks, const GemmTerm* d_terms, cudaStream_t s) {
+  if (N <= 1) gemv_kernel<T, 1><<<g, NT, 0, s>>>(d_tasks, d_terms);
+  else if (N <= 2) gemv_kernel<T, 2><<<g, NT, 0, s>>>(d_tasks, d_terms);
+  else if (N <= 4) gemv_kernel<T, 4><<<g, NT, 0, s>>>(d_tasks, d_terms);
+  else gemv_kernel<T, 8><<<g, NT, 0, s>>>(d_tasks, d_terms);
 }
 
 template <typename T, bool F64IN>
@@ -227,8 +258,8 @@ void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
   if (maxN <= GV_MAXN && !inputs_f64) {
     dim3 g(ntasks, (maxM + GV_ROWS - 1) / GV_ROWS);
     ProfScope ps(p == Prec::F64 ? "gemv_f64" : "gemv_f32", s);
-    if (p == Prec::F64) gemv_kernel<double><<<g, NT, 0, s>>>(d_tasks, d_terms);
-    else gemv_kernel<float><<<g, NT, 0, s>>>(d_tasks, d_terms);
+    if (p == Prec::F64) gemv_dispatch<double>(maxN, g, d_tasks, d_terms, s);
+    else gemv_dispatch<float>(maxN, g, d_tasks, d_terms, s);
     H2_LAUNCH_CHECK();
     return;
   }

@@ -34,32 +34,41 @@ __global__ void __launch_bounds__(NT) symv_pairs_kernel(const SymPairTask* __res
 #pragma unroll
     for (int c = 0; c < NR; ++c) u[t][c] = (T)0;
   T* vout = reinterpret_cast<T*>(part) + tk.vo;
-  for (int j = warp; j < nJ; j += 8) {
-    const T* col = A + (long long)j * tk.lda;
-    T a[8];
+  // four columns per warp per pass: 32 independent loads per lane in flight
+  for (int j0 = warp * 4; j0 < nJ; j0 += 32) {
+    T a[4][8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      int i = lane + 32 * t;
-      a[t] = i < nI ? col[i] : (T)0;
-    }
-    T v[NR];
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q;
+      const T* col = A + (long long)min(j, nJ - 1) * tk.lda;
 #pragma unroll
-    for (int c = 0; c < NR; ++c) v[c] = (T)0;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      int i = lane + 32 * t;
-#pragma unroll
-      for (int c = 0; c < NR; ++c) {
-        v[c] = fma(a[t], xI[i][c], v[c]);
-        u[t][c] = fma(a[t], xJ[j][c], u[t][c]);
+      for (int t = 0; t < 8; ++t) {
+        int i = lane + 32 * t;
+        a[q][t] = (i < nI && j < nJ) ? col[i] : (T)0;
       }
     }
 #pragma unroll
-    for (int c = 0; c < NR; ++c) {
-      T s = v[c];
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q;
+      T v[NR];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) vout[j + c * nJ] = s;
+      for (int c = 0; c < NR; ++c) v[c] = (T)0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        int i = lane + 32 * t;
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+          v[c] = fma(a[q][t], xI[i][c], v[c]);
+          u[t][c] = fma(a[q][t], (j < nJ) ? xJ[j][c] : (T)0, u[t][c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        T s = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0 && j < nJ) vout[j + c * nJ] = s;
+      }
     }
   }
 #pragma unroll
