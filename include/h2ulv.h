@@ -159,7 +159,7 @@ h2_status h2_logdet(h2_handle h, double* log_abs_det, int32_t* sign);
  * between latency-critical launches).  The paper has no counterpart: it is
  * an interface addition of this library.  Same result as h2_logdet (host
  * arrays of length P for a batched handle).
- *   - Scratch: a fixed 768 KB device array inside the library (task
+ *   - Scratch: a fixed 1 MB device array inside the library (task
  *     descriptors and per-block partials), held by every device that loads
  *     the library until the process exits; nothing is allocated per call.
  *   - Limit: at most 16384 factored blocks per tree height; larger handles
@@ -181,6 +181,56 @@ h2_status h2_stats(h2_handle h, char* json, size_t cap);
  * launches, summed event time (ms) and the algorithmic flops and bytes its
  * callers declared.  reset = 1 clears the counters first. */
 h2_status h2_profile(int32_t enable, int32_t reset);
+
+/* ---------------------------------------------------------------------
+ * Rank predictor (an interface addition; the paper has no learned part).
+ * A 3-layer MLP (8 box features -> 64 -> 64 -> 1, tanh, FP32) trained on the
+ * GPU by the library's own forward / backward / Adam kernels on
+ * (box features -> rank of the pivoted QR of the block row) pairs.  Given
+ * to a handle, it predicts every box's rank before the basis pass so that
+ * the next level's block storage is sized and allocated while the basis
+ * kernels run; the pivoted QR still decides every rank, and a box whose
+ * rank exceeds its prediction plus the margin falls back to exact sizing.
+ * Parameter layout: W1 (64 x 8, row-major), b1 (64), W2 (64 x 64), b2 (64),
+ * w3 (64), b3 (1).  Arrays may be host or device pointers. */
+typedef struct h2_mlp_* h2_mlp;
+
+/* Number of parameters for n_features inputs (4801 for 8). */
+int32_t h2_mlp_param_count(int32_t n_features);
+
+/* Create a predictor from initial parameters (caller-drawn, length
+ * h2_mlp_param_count(8)); n_features must be 8. */
+h2_status h2_mlp_create(int32_t n_features, const float* init_params, void* stream, h2_mlp* out);
+
+/* steps full-batch Adam steps on mean((f(X) - T)^2); X is B x 8 row-major,
+ * T has B targets; final_loss (host, may be NULL) receives the loss after
+ * training. */
+h2_status h2_mlp_train(h2_mlp m, const float* X, const float* T, int32_t B, int32_t steps, float lr,
+                       float* final_loss);
+
+/* Y = f(X) for B samples. */
+h2_status h2_mlp_forward(h2_mlp m, const float* X, int32_t B, float* Y);
+
+/* Gradient of mean((f(X) - T)^2) with respect to the parameters (length
+ * h2_mlp_param_count) and the loss; parameters are not changed. */
+h2_status h2_mlp_gradient(h2_mlp m, const float* X, const float* T, int32_t B, float* grad, float* loss);
+
+/* Copy the current parameters out. */
+h2_status h2_mlp_params(h2_mlp m, float* out);
+
+const char* h2_mlp_last_error(void);
+void h2_mlp_destroy(h2_mlp m);
+
+/* Features of every box at one height (8 floats per box, row-major) and,
+ * after h2_factor, the rank the pivoted QR chose for each box (training
+ * targets).  features or ranks may be NULL; *nboxes receives the count. */
+h2_status h2_box_features(h2_handle h, int32_t height, float* features, int32_t* ranks, int32_t* nboxes);
+
+/* Use m (kept by reference; NULL detaches) to size each level's storage
+ * before its basis pass; a box is covered when its rank is at most
+ * (1 + margin) times its predicted rank plus 4.  h2_stats reports hits,
+ * misses and the bytes sized up front. */
+h2_status h2_set_rank_predictor(h2_handle h, h2_mlp m, double margin);
 
 /* Thread-local message of the last failed call on this thread. */
 const char* h2_last_error(void);

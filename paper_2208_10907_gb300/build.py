@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libh2ulv.so")
-SOURCES = ["k_gemm.cu", "k_dense.cu", "k_tc.cu", "k_mlp.cu", "h2_api.cu", "h2_tree.cpp", "h2_prof.cpp", "k_symv.cu"]
+SOURCES = ["k_gemm.cu", "k_dense.cu", "k_tc.cu", "k_mlp.cu", "h2_api.cu", "h2_tree.cpp", "h2_prof.cpp", "k_symv.cu", "h2_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

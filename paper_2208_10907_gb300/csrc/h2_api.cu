@@ -19,6 +19,7 @@
 
 #include "../../include/h2ulv.h"
 #include "h2_common.cuh"
+#include "h2_mlp.h"
 #include "h2_prof.h"
 #include "h2_tree.h"
 
@@ -565,11 +566,32 @@ struct Handle {
   std::map<int, std::shared_ptr<SolvePlans>> plans;
   double t_construct_ms = 0, t_factor_ms = 0;
   std::vector<double> level_ms;
+  // rank predictor (optional)
+  const Mlp* predictor = nullptr;
+  double pred_margin = 0.15;
+  long long pred_hits = 0, pred_misses = 0;
+  double pred_bytes = 0, worst_bytes = 0, exact_bytes = 0;
   std::string stats_extra;
 };
 
 static Points points(const Handle& h) {
   return Points{h.px.as<double>(), h.py.as<double>(), h.pz.as<double>()};
+}
+
+// Predictor features of every box at height H (8 per box).
+static void height_features(const Handle& h, int H, std::vector<float>& F) {
+  const Height& ht = h.hs[H];
+  F.assign((size_t)ht.nb * MLP_FEATURES, 0.f);
+  std::vector<int64_t> samp;
+  for (int g = 0; g < ht.nb; ++g) {
+    const BoxRef& b = ht.ref[g];
+    const Problem& pb = h.probs[b.prob];
+    const Box& bx = pb.t.boxes[b.level][b.local];
+    far_samples(pb.t, b.level, b.local, h.opt.far_s0, h.opt.far_smin, samp);
+    int n = ht.n.empty() ? (int)(bx.e - bx.s) : ht.n[g];
+    box_features(n, bx.lo, bx.hi, (int)ht.near[g].size(), (int)ht.far[g].size(), H, (int)samp.size(),
+                 &F[(size_t)g * MLP_FEATURES]);
+  }
 }
 
 static bool is_device_ptr(const void* p) {
@@ -1017,7 +1039,6 @@ static PlanP build_matvec_plan(Handle& h, const double* x, double* y, int nrhs) 
 // Blocked right-looking LU with partial pivoting of the dense top-level
 // matrix (eq. BLR2final), then its inverse (the root solve becomes a GEMM).
 static void root_factor(Handle& h, Root& rt, int spd) {
-  (void)spd;
   cudaStream_t s = h.s;
   const int n = rt.n;
   if (n == 0) return;
@@ -1029,7 +1050,7 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   const int NB = 64;
   for (int k = 0; k < n; k += NB) {
     int nb = std::min(NB, n - k);
-    std::vector<LuTask> lt{LuTask{A + k + (size_t)k * n, n - k, nb, n, piv + k, info}};
+    std::vector<LuTask> lt{LuTask{A + k + (size_t)k * n, n - k, nb, n, piv + k, info, spd ? 1 : 0}};
     run_getrf(Prec::F64, lt, sc);
     // pivots are panel-relative: convert to global rows and apply to the
     // columns left and right of the panel
@@ -1058,10 +1079,12 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   int hinfo = 0;
   H2_CUDA(cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, s));
   H2_CUDA(cudaStreamSynchronize(s));
-  if (hinfo != 0) throw StatusError(H2_ERR_SINGULAR, "zero pivot in the top-level LU");
+  if (hinfo != 0)
+    throw StatusError(spd ? H2_ERR_NOT_SPD : H2_ERR_SINGULAR,
+                      spd ? "non-positive pivot in the top-level Cholesky" : "zero pivot in the top-level LU");
   // log-determinant
   {
-    std::vector<LuTask> lt{LuTask{A, n, n, n, piv, nullptr}};
+    std::vector<LuTask> lt{LuTask{A, n, n, n, piv, nullptr, 0}};
     double* o = (double*)sc.alloc(16);
     launch_logdet_lu(sc.up(lt), 1, o, o + 1, false, s);
     double ho[2];
@@ -1240,6 +1263,50 @@ static void factor(Handle& h, int precision, int spd) {
         if (ht.near[g][q] == g) return (int)q;
       return -1;
     };
+    // ---------------- 0. predicted ranks: size the next level up front -----
+    Height* upp = (H + 1 < h.Hmax) ? &h.hs[H + 1] : nullptr;
+    std::vector<int> rcap;
+    DBufP Apre;                          // next-level storage sized from predictions
+    std::vector<std::vector<size_t>> pre_off;
+    std::vector<int> pre_ld;
+    if (h.predictor && upp) {
+      prof_tag("predict");
+      std::vector<float> Fh;
+      height_features(h, H, Fh);
+      const Mlp& m = *h.predictor;
+      float* dX = (float*)sc.alloc(Fh.size() * 4);
+      float* dH1 = (float*)sc.alloc((size_t)nb * MLP_WIDTH * 4);
+      float* dH2 = (float*)sc.alloc((size_t)nb * MLP_WIDTH * 4);
+      float* dY = (float*)sc.alloc((size_t)nb * 4);
+      H2_CUDA(cudaMemcpyAsync(dX, Fh.data(), Fh.size() * 4, cudaMemcpyHostToDevice, s));
+      mlp_forward(m.prm, m.F, dX, nb, dH1, dH2, dY, nullptr, nullptr, s);
+      std::vector<float> yh(nb);
+      H2_CUDA(cudaMemcpyAsync(yh.data(), dY, (size_t)nb * 4, cudaMemcpyDeviceToHost, s));
+      H2_CUDA(cudaStreamSynchronize(s));
+      rcap.resize(nb);
+      for (int g = 0; g < nb; ++g) {
+        double rh = std::max(0.0, (double)yh[g]) * h.opt.max_rank;
+        int c = (int)std::ceil(rh * (1.0 + h.pred_margin)) + 4;
+        rcap[g] = std::max(1, std::min({c, n[g], h.opt.max_rank}));
+      }
+      std::vector<int> ncap(upp->nb, 0);
+      for (int g = 0; g < nb; ++g)
+        if (ht.parent[g] >= 0) ncap[ht.parent[g]] += rcap[g];
+      size_t tot = 0, worst = 0;
+      pre_off.assign(upp->nb, {});
+      pre_ld = ncap;
+      for (int pg = 0; pg < upp->nb; ++pg)
+        for (int qg : upp->near[pg]) {
+          pre_off[pg].push_back(tot);
+          if (pg <= qg) {
+            tot += (size_t)ncap[pg] * ncap[qg];
+            worst += (size_t)(2 * h.opt.max_rank) * (2 * h.opt.max_rank);
+          }
+        }
+      Apre = std::make_shared<DBuf>(std::max<size_t>(1, tot) * ws);
+      h.pred_bytes += (double)tot * ws;
+      h.worst_bytes += (double)worst * ws;
+    }
     // ---------------- 1. fill-ins (Sec. III-B) --------------------------
     prof_tag("fillin");
     std::vector<int> has_lu(nb, 0);
@@ -1262,7 +1329,7 @@ static void factor(Handle& h, int precision, int spd) {
         int dq = diag_q(g);
         void* dst = (char*)LUK + so[g] * ws;
         ct.push_back(CopyTask{Ablk[g][dq].ptr, dst, n[g], n[g], Ablk[g][dq].ld, n[g]});
-        lu.push_back(LuTask{dst, n[g], n[g], n[g], pivK + (size_t)g * 256, finfo});
+        lu.push_back(LuTask{dst, n[g], n[g], n[g], pivK + (size_t)g * 256, finfo, 0});
         std::vector<GemmTerm> ts;
         for (size_t q = 0; q < ht.near[g].size(); ++q) {
           int j = ht.near[g][q];
@@ -1513,19 +1580,38 @@ static void factor(Handle& h, int precision, int spd) {
           po[pg].push_back(tot);
           if (pg <= qg) tot += (size_t)up->n[pg] * up->n[qg];
         }
-      if (h.opt.hbm_budget_bytes > 0 && (int64_t)(tot * ws) > h.opt.hbm_budget_bytes)
-        throw StatusError(H2_ERR_BUDGET, "level near blocks need " + std::to_string(tot * ws) + " bytes");
-      Anext_buf = std::make_shared<DBuf>(std::max<size_t>(1, tot) * ws);
+      h.exact_bytes += (double)tot * ws;
+      bool hit = false;
+      if (Apre) {
+        hit = true;
+        for (int g = 0; g < nb && hit; ++g) hit = r[g] <= rcap[g];
+        if (hit) ++h.pred_hits;
+        else ++h.pred_misses;
+      }
+      std::vector<int> lds(up->nb);
+      if (hit) {
+        // the predicted capacities cover every rank: keep the storage that
+        // was allocated before the basis pass (leading dimension = capacity)
+        Anext_buf = Apre;
+        po = pre_off;
+        lds = pre_ld;
+      } else {
+        Apre.reset();
+        if (h.opt.hbm_budget_bytes > 0 && (int64_t)(tot * ws) > h.opt.hbm_budget_bytes)
+          throw StatusError(H2_ERR_BUDGET, "level near blocks need " + std::to_string(tot * ws) + " bytes");
+        Anext_buf = std::make_shared<DBuf>(std::max<size_t>(1, tot) * ws);
+        lds = up->n;
+      }
       Anext.assign(up->nb, {});
       for (int pg = 0; pg < up->nb; ++pg)
         for (size_t q = 0; q < up->near[pg].size(); ++q) {
           int qg = up->near[pg][q];
           if (pg <= qg) {
-            Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[pg][q] * ws, up->n[pg], 0});
+            Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[pg][q] * ws, lds[pg], 0});
           } else {
             const auto& nl = up->near[qg];
             size_t qq = std::find(nl.begin(), nl.end(), pg) - nl.begin();
-            Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[qg][qq] * ws, up->n[qg], 1});
+            Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[qg][qq] * ws, lds[qg], 1});
           }
         }
     }
@@ -1651,7 +1737,7 @@ static void factor(Handle& h, int precision, int spd) {
       for (int g = 0; g < nb; ++g) {
         if (m[g] == 0) continue;
         double* Sg = S + off[g];
-        lu.push_back(LuTask{Sg, m[g], m[g], n[g], ht.pivRR->as<int>() + ht.pv_off[g], info});
+        lu.push_back(LuTask{Sg, m[g], m[g], n[g], ht.pivRR->as<int>() + ht.pv_off[g], info, spd ? 1 : 0});
         trs.push_back(TrsmTask{Sg, Sg + (size_t)m[g] * n[g], m[g], r[g], n[g], n[g], ht.pivRR->as<int>() + ht.pv_off[g]});
         // (L^SR)^T = U^-T (S^SR)^T: transpose S^SR (r x m) into Lt (m x r)
         tr.push_back(CopyTask{Sg + m[g], ht.Lt->as<double>() + ht.lt_off[g], m[g], r[g], n[g], m[g]});
@@ -1713,7 +1799,9 @@ static void factor(Handle& h, int precision, int spd) {
     int hinfo = 0;
     H2_CUDA(cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaStreamSynchronize(s));
-    if (hinfo != 0) throw StatusError(H2_ERR_SINGULAR, "zero pivot in a redundant-block LU");
+    if (hinfo != 0)
+      throw StatusError(spd ? H2_ERR_NOT_SPD : H2_ERR_SINGULAR,
+                        spd ? "non-positive pivot in a redundant-block Cholesky" : "zero pivot in a redundant-block LU");
     // ---------------- 5. next height: T = blockdiag(W_a, W_b) ---------
     prof_tag("merge");
     if (up) {
@@ -2084,6 +2172,8 @@ h2_status h2_factor(h2_handle H, int32_t precision, int32_t spd) {
     Handle& h = H->h;
     h.factored = false;
     h.plans.clear();
+    h.pred_hits = h.pred_misses = 0;
+    h.pred_bytes = h.worst_bytes = h.exact_bytes = 0;
     double t0 = now_ms();
     factor(h, precision, spd);
     h.t_factor_ms = now_ms() - t0;
@@ -2383,7 +2473,7 @@ h2_status h2_logdet(h2_handle H, double* log_abs_det, int32_t* sign) {
       for (int g = 0; g < ht.nb; ++g) {
         int m = ht.n[g] - ht.r[g];
         if (m == 0) continue;
-        lt.push_back(LuTask{ht.S->as<double>() + ht.q_off[g], m, m, ht.n[g], ht.pivRR->as<int>() + ht.pv_off[g], nullptr});
+        lt.push_back(LuTask{ht.S->as<double>() + ht.q_off[g], m, m, ht.n[g], ht.pivRR->as<int>() + ht.pv_off[g], nullptr, 0});
         who.push_back(ht.ref[g].prob);
       }
       if (lt.empty()) continue;
@@ -2445,7 +2535,7 @@ h2_status h2_logdet_noalloc(h2_handle H, double* log_abs_det, int32_t* sign) {
       for (int g = 0; g < ht.nb; ++g) {
         int m = ht.n[g] - ht.r[g];
         if (m == 0) continue;
-        lt.push_back(LuTask{ht.S->as<double>() + ht.q_off[g], m, m, ht.n[g], ht.pivRR->as<int>() + ht.pv_off[g], nullptr});
+        lt.push_back(LuTask{ht.S->as<double>() + ht.q_off[g], m, m, ht.n[g], ht.pivRR->as<int>() + ht.pv_off[g], nullptr, 0});
         who.push_back(ht.ref[g].prob);
       }
       if (lt.empty()) continue;
@@ -2496,7 +2586,10 @@ h2_status h2_stats(h2_handle H, char* json, size_t cap) {
     }
     o << "],\"roots\":[";
     for (size_t p = 0; p < h.probs.size(); ++p) o << (p ? "," : "") << h.probs[p].root.n;
-    o << "],\"launches\":" << prof().total_launches << ",\"kernels\":{";
+    o << "],\"predictor\":{\"attached\":" << (h.predictor ? 1 : 0) << ",\"hits\":" << h.pred_hits
+      << ",\"misses\":" << h.pred_misses << ",\"presized_bytes\":" << h.pred_bytes
+      << ",\"worstcase_bytes\":" << h.worst_bytes << ",\"exact_bytes\":" << h.exact_bytes << "}";
+    o << ",\"launches\":" << prof().total_launches << ",\"kernels\":{";
     prof().resolve();
     bool first = true;
     for (auto& kv : prof().stats) {
@@ -2511,6 +2604,37 @@ h2_status h2_stats(h2_handle H, char* json, size_t cap) {
     std::memcpy(json, sj.data(), n);
     json[n] = 0;
   });
+}
+
+h2_status h2_box_features(h2_handle H, int32_t height, float* features, int32_t* ranks, int32_t* nboxes) {
+  if (!H || height < 0 || height >= H->h.Hmax) {
+    g_err = "invalid h2_box_features arguments";
+    return H2_ERR_ARG;
+  }
+  return guard([&] {
+    Handle& h = H->h;
+    const Height& ht = h.hs[height];
+    if (nboxes) *nboxes = ht.nb;
+    if (features) {
+      std::vector<float> F;
+      height_features(h, height, F);
+      std::memcpy(features, F.data(), F.size() * 4);
+    }
+    if (ranks) {
+      if (!h.factored) throw StatusError(H2_ERR_STATE, "ranks need h2_factor first");
+      for (int g = 0; g < ht.nb; ++g) ranks[g] = ht.r[g];
+    }
+  });
+}
+
+h2_status h2_set_rank_predictor(h2_handle H, h2_mlp m, double margin) {
+  if (!H || !(margin >= 0)) {
+    g_err = "invalid h2_set_rank_predictor arguments";
+    return H2_ERR_ARG;
+  }
+  H->h.predictor = m ? reinterpret_cast<const Mlp*>(m) : nullptr;
+  H->h.pred_margin = margin;
+  return H2_OK;
 }
 
 h2_status h2_profile(int32_t enable, int32_t reset) {

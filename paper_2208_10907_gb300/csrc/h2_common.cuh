@@ -102,6 +102,7 @@ struct LuTask {        // in-place LU with partial pivoting of an m x nc panel
   int m, nc, lda;
   int* piv;            // nc pivots (0-based row index within the panel)
   int* info;           // set to k+1 at the first zero pivot (if non-null)
+  int spd;             // 1: no pivoting, every pivot must be > 0 (symmetric positive definite)
 };
 
 struct TrsmTask {      // B <- op(A)^-1 B, A n x n triangular, B n x nrhs

@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(NT) getrf_kernel(const LuTask* __restrict__ ta
     T pv;
     int p;
     block_argmax(best, bi, s_val, s_idx, pv, p);
+    if (tk.spd) p = k;       // symmetric positive definite: no pivoting
     if (p < k || p >= m) {   // every candidate was NaN: keep the row, flag the panel
       p = k;
       if (threadIdx.x == 0 && tk.info) atomicCAS(tk.info, 0, k + 1);
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(NT) getrf_kernel(const LuTask* __restrict__ ta
     }
     __syncthreads();
     T akk = A[k + (long long)k * lda];
-    if (akk == (T)0 || akk != akk) {
+    if (akk == (T)0 || akk != akk || (tk.spd && akk < (T)0)) {
       if (!singular && threadIdx.x == 0 && tk.info) atomicCAS(tk.info, 0, k + 1);
       singular = true;
       __syncthreads();

@@ -21,7 +21,9 @@ H2_FP64, H2_MIXED = 0, 1
 KERNEL_KIND = {"laplace": H2_K_LAPLACE, "yukawa": H2_K_YUKAWA, "matern32": H2_K_MATERN32}
 
 EXPORTED = ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_matvec",
-            "h2_logdet", "h2_logdet_noalloc", "h2_stats", "h2_profile", "h2_last_error", "h2_destroy")
+            "h2_logdet", "h2_logdet_noalloc", "h2_stats", "h2_profile", "h2_last_error", "h2_destroy",
+            "h2_mlp_param_count", "h2_mlp_create", "h2_mlp_train", "h2_mlp_forward", "h2_mlp_gradient",
+            "h2_mlp_params", "h2_mlp_last_error", "h2_mlp_destroy", "h2_box_features", "h2_set_rank_predictor")
 
 
 class h2_kernel(ctypes.Structure):
@@ -63,6 +65,21 @@ def lib():
         L.h2_logdet_noalloc.argtypes = [vp, vp, vp]
         L.h2_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         L.h2_profile.argtypes = [i32, i32]
+        fp = ctypes.c_float
+        L.h2_mlp_param_count.argtypes = [i32]
+        L.h2_mlp_param_count.restype = i32
+        L.h2_mlp_create.argtypes = [i32, vp, vp, ctypes.POINTER(vp)]
+        L.h2_mlp_train.argtypes = [vp, vp, vp, i32, i32, fp, vp]
+        L.h2_mlp_forward.argtypes = [vp, vp, i32, vp]
+        L.h2_mlp_gradient.argtypes = [vp, vp, vp, i32, vp, vp]
+        L.h2_mlp_params.argtypes = [vp, vp]
+        L.h2_mlp_last_error.restype = ctypes.c_char_p
+        L.h2_mlp_destroy.argtypes = [vp]
+        L.h2_box_features.argtypes = [vp, i32, vp, vp, ctypes.POINTER(i32)]
+        L.h2_set_rank_predictor.argtypes = [vp, vp, dp]
+        for f in ("h2_mlp_create", "h2_mlp_train", "h2_mlp_forward", "h2_mlp_gradient", "h2_mlp_params",
+                  "h2_box_features", "h2_set_rank_predictor"):
+            getattr(L, f).restype = ctypes.c_int
         L.h2_last_error.restype = ctypes.c_char_p
         L.h2_destroy.argtypes = [vp]
         for f in ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_matvec", "h2_logdet",
@@ -156,6 +173,72 @@ def h2_stats(h, cap=1 << 16):
 
 def h2_profile(enable, reset=0):
     _check(lib().h2_profile(int(enable), int(reset)))
+
+
+def _check_mlp(st):
+    if st != H2_OK:
+        raise H2Error(st, lib().h2_mlp_last_error().decode())
+
+
+def h2_mlp_param_count(n_features=8):
+    return lib().h2_mlp_param_count(n_features)
+
+
+def h2_mlp_create(init_params, stream=None):
+    p = np.ascontiguousarray(init_params, dtype=np.float32)
+    m = ctypes.c_void_p()
+    _check_mlp(lib().h2_mlp_create(8, ctypes.c_void_p(p.ctypes.data), ctypes.c_void_p(stream or 0), ctypes.byref(m)))
+    return m
+
+
+def h2_mlp_train(m, X, T, steps, lr=1e-3):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    loss = ctypes.c_float(0)
+    _check_mlp(lib().h2_mlp_train(m, ctypes.c_void_p(X.ctypes.data), ctypes.c_void_p(T.ctypes.data), len(T),
+                                  int(steps), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def h2_mlp_forward(m, X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.zeros(len(X), dtype=np.float32)
+    _check_mlp(lib().h2_mlp_forward(m, ctypes.c_void_p(X.ctypes.data), len(X), ctypes.c_void_p(Y.ctypes.data)))
+    return Y
+
+
+def h2_mlp_gradient(m, X, T):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    g = np.zeros(h2_mlp_param_count(), dtype=np.float32)
+    loss = ctypes.c_float(0)
+    _check_mlp(lib().h2_mlp_gradient(m, ctypes.c_void_p(X.ctypes.data), ctypes.c_void_p(T.ctypes.data), len(T),
+                                     ctypes.c_void_p(g.ctypes.data), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def h2_mlp_params(m):
+    p = np.zeros(h2_mlp_param_count(), dtype=np.float32)
+    _check_mlp(lib().h2_mlp_params(m, ctypes.c_void_p(p.ctypes.data)))
+    return p
+
+
+def h2_mlp_destroy(m):
+    lib().h2_mlp_destroy(m)
+
+
+def h2_box_features(h, height, with_ranks=False):
+    nb = ctypes.c_int32(0)
+    _check(lib().h2_box_features(h, int(height), None, None, ctypes.byref(nb)))
+    F = np.zeros((nb.value, 8), dtype=np.float32)
+    R = np.zeros(nb.value, dtype=np.int32) if with_ranks else None
+    _check(lib().h2_box_features(h, int(height), ctypes.c_void_p(F.ctypes.data),
+                                 ctypes.c_void_p(R.ctypes.data) if with_ranks else None, ctypes.byref(nb)))
+    return (F, R) if with_ranks else F
+
+
+def h2_set_rank_predictor(h, m, margin=0.15):
+    _check(lib().h2_set_rank_predictor(h, m, float(margin)))
 
 
 def h2_destroy(h):

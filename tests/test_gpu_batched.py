@@ -1,0 +1,69 @@
+"""Batched handle (several independent problems of different sizes and
+depths factored and solved height by height in shared launches): every
+problem's refined solution and log-determinant against the oracle and
+against its own single-problem handle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import h2ulv_oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2208_10907_gb300 import h2ulv as H  # noqa: E402
+
+
+def problems():
+    rng = np.random.default_rng(100)
+    out = []
+    for k, n in enumerate([3000, 700, 5200, 130, 2049]):
+        r = np.random.default_rng(100 + k)
+        geo = k % 3
+        if geo == 0:
+            X = synth.cube_surface(n, r)
+        elif geo == 1:
+            X = synth.sphere_surface(n, r)
+        else:
+            X = synth.ellipsoid_surface(n, r, tuple(0.5 + 1.5 * r.random(3)))
+        out.append(X)
+    return out
+
+
+@pytest.mark.parametrize("precision", [H.H2_FP64, H.H2_MIXED])
+def test_batched_matches_oracle_and_single(precision):
+    Xs = problems()
+    opt = H.make_options(leaf=128, tol=1e-8, max_rank=100)
+    kern = H.make_kernel("laplace")
+    hb = H.h2_construct_batched([torch.from_numpy(X).cuda() for X in Xs], kern, opt)
+    try:
+        H.h2_factor(hb, precision)
+        Ns = [len(X) for X in Xs]
+        off = np.concatenate([[0], np.cumsum(Ns)])
+        nrhs = 3
+        B = np.zeros((off[-1], nrhs))
+        for p, N in enumerate(Ns):
+            B[off[p]:off[p + 1]] = synth.rhs(N, nrhs, 50 + p)
+        Bc = np.ascontiguousarray(B.T)                       # column-major stacked
+        Xc = np.zeros_like(Bc)
+        st, ach, it = H.h2_solve(hb, Bc, Xc, nrhs, off[-1], 1e-10, 40)
+        assert st == H.H2_OK and np.all(ach <= 1e-10), (st, ach)
+        ldb, sgb = H.h2_logdet(hb, len(Xs))
+        for p, X in enumerate(Xs):
+            pb = O.Problem(X, "laplace", 128, 1.0, 1e-8, 100)
+            xo, _, _ = O.refine(O.H2Operator(pb), O.ULVFactor(pb), B[off[p]:off[p + 1]], 1e-10, 40)
+            xg = Xc.T[off[p]:off[p + 1]]
+            assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+            # the same problem alone
+            h1 = H.h2_construct(torch.from_numpy(X).cuda(), len(X), kern, opt)
+            try:
+                H.h2_factor(h1, precision)
+                l1, s1 = H.h2_logdet(h1)
+                assert s1[0] == sgb[p]
+                assert abs(l1[0] - ldb[p]) <= 1e-9 * abs(l1[0])
+            finally:
+                H.h2_destroy(h1)
+    finally:
+        H.h2_destroy(hb)

@@ -118,3 +118,28 @@ def test_host_buffers_multiple_rhs():
         assert err <= 1e-8, err
     finally:
         H.h2_destroy(h)
+
+
+def test_spd_path_matches_oracle_cholesky():
+    """spd = 1: redundant blocks and the root are factored without pivoting
+    with positive pivots (the LDL^T form of the Cholesky-ULV); the log-det
+    equals the oracle's Cholesky factorization's."""
+    X, pb, op, fac = oracle_case("sphereball4k_yukawa")
+    _, kern, leaf, tol, mr = CASES["sphereball4k_yukawa"]
+    facs = O.ULVFactor(pb, spd=True)
+    N = len(X)
+    b = synth.rhs(N, 1, 3)[:, 0].copy()
+    xo, _, _ = O.refine(op, facs, b, 1e-10, 30)
+    h = gpu_handle(X, kern, leaf, tol, mr)
+    try:
+        H.h2_factor(h, H.H2_FP64, 1)
+        ld, sg = H.h2_logdet(h)
+        lo, so = facs.logdet()
+        assert sg[0] == 1 and abs(ld[0] - lo) <= 1e-9 * abs(lo)
+        bt = torch.from_numpy(b).cuda()
+        xt = torch.zeros_like(bt)
+        st, ach, it = H.h2_solve(h, bt, xt, 1, N, 1e-10, 30)
+        assert st == H.H2_OK
+        assert np.linalg.norm(xt.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
+    finally:
+        H.h2_destroy(h)
