@@ -62,7 +62,9 @@ def test_batched_matches_oracle_and_single(precision):
                 H.h2_factor(h1, precision)
                 l1, s1 = H.h2_logdet(h1)
                 assert s1[0] == sgb[p]
-                assert abs(l1[0] - ldb[p]) <= 1e-9 * abs(l1[0])
+                # FP64: same arithmetic per box; mixed: FP32-accurate factors
+                rel = 1e-9 if precision == H.H2_FP64 else 1e-6
+                assert abs(l1[0] - ldb[p]) <= rel * abs(l1[0])
             finally:
                 H.h2_destroy(h1)
     finally:
