@@ -197,11 +197,14 @@ static void validate(const std::vector<InterpTask>& v, size_t es) {
 struct GemmBatch {
   std::vector<GemmTask> tasks;
   std::vector<GemmTerm> terms;
-  int maxM = 0, maxN = 0;
+  int maxM = 0, maxN = 0, ksum = 0;
   double flops = 0.0, bytes = 0.0;
   void add(void* C, int ldc, int M, int N, double alpha, double beta, const void* Cin, int ldcin,
            const std::vector<GemmTerm>& ts) {
     if (M <= 0 || N <= 0) return;
+    int kt = 0;
+    for (const GemmTerm& g : ts) kt += std::max(0, g.K);
+    ksum = std::max(ksum, kt);
     GemmTask t;
     t.C = C;
     t.Cin = Cin;
@@ -243,7 +246,7 @@ struct GemmBatch {
       std::vector<GemmTask> sub(tasks.begin() + o, tasks.begin() + o + cnt);
       GemmTask* dt = sc.up(sub);
       if (o == 0) prof_note(flops, bytes * esz(p));
-      launch_gemm(p, dt, dm, (int)cnt, maxM, maxN, sc.s);
+      launch_gemm(p, dt, dm, (int)cnt, maxM, maxN, sc.s, false, ksum);
     }
   }
 };
@@ -340,6 +343,7 @@ struct Plan {
     o.n = (int)gb.tasks.size();
     o.a = gb.maxM;
     o.b = gb.maxN;
+    o.ld = gb.ksum;
     o.tag = cur_tag;
     ops.push_back(o);
   }
@@ -420,7 +424,8 @@ struct Plan {
   void issue(cudaStream_t st) const {
     for (const Op& o : ops) {
       prof_tag(o.tag);
-      if (o.kind == 0) launch_gemm(o.p, (const GemmTask*)o.tasks, (const GemmTerm*)o.terms, o.n, o.a, o.b, st);
+      if (o.kind == 0)
+        launch_gemm(o.p, (const GemmTask*)o.tasks, (const GemmTerm*)o.terms, o.n, o.a, o.b, st, false, (int)o.ld);
       else if (o.kind == 1) launch_trsm(o.p, o.f1, o.f2, o.f3, (const TrsmTask*)o.tasks, o.n, o.a, st);
       else if (o.kind == 2) launch_copy(o.p, o.p2, o.f1, (const CopyTask*)o.tasks, o.n, o.a, o.b, st);
       else if (o.kind == 3) launch_symv_pairs((const SymPairTask*)o.tasks, o.n, o.x, o.ld, o.y, o.a, st);
@@ -2589,6 +2594,7 @@ h2_status h2_stats(h2_handle H, char* json, size_t cap) {
     o << "],\"predictor\":{\"attached\":" << (h.predictor ? 1 : 0) << ",\"hits\":" << h.pred_hits
       << ",\"misses\":" << h.pred_misses << ",\"presized_bytes\":" << h.pred_bytes
       << ",\"worstcase_bytes\":" << h.worst_bytes << ",\"exact_bytes\":" << h.exact_bytes << "}";
+    o << ",\"autotune\":" << autotune_report();
     o << ",\"launches\":" << prof().total_launches << ",\"kernels\":{";
     prof().resolve();
     bool first = true;

@@ -193,9 +193,11 @@ struct GatherTask {    // y[s : s+n] = sum of partials p0 .. p0+np-1
 // ---------------------------------------------------------------------------
 enum class Prec { F64 = 0, F32 = 1 };
 
-// Terms carry their own transposition flags (GemmTerm::flags).
+// Terms carry their own transposition flags (GemmTerm::flags).  ksum = the
+// largest summed K of a task (selects the autotuned kernel for FP32 data).
 void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
-                 int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64 = false);
+                 int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64 = false, int ksum = 0);
+std::string autotune_report();
 void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s);
 void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks,
                  int maxnrhs, cudaStream_t s);

@@ -8,6 +8,9 @@
 #include "h2_common.cuh"
 #include "h2_prof.h"
 
+#include <map>
+#include <string>
+
 namespace h2 {
 
 namespace {
@@ -242,18 +245,119 @@ void dispatch(const GemmTask* d_tasks, const GemmTerm* d_terms, dim3 grid, cudaS
 void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, int ntasks, int maxM, int maxN,
                     cudaStream_t s);
 
-// FP32-class products go to the tcgen05 split-3xTF32 kernel unless H2_TC=0.
-static bool tc_enabled() {
-  static int v = -1;
-  if (v < 0) {
+// FP32-class products go to the tcgen05 split-3xTF32 kernel unless H2_TC=0
+// (H2_TC=1 forces it); by default the autotuner below decides per shape.
+static int tc_mode() {
+  static int v = -2;
+  if (v == -2) {
     const char* e = getenv("H2_TC");
-    v = (e && e[0] == '0') ? 0 : 1;
+    v = !e ? -1 : (e[0] == '0' ? 0 : 1);
   }
-  return v == 1;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: for each shape bucket (output rows, output columns, summed K of
+// a task, each rounded up to a power of two) the tcgen05 kernel and the SIMT
+// kernel are timed once on scratch data of that shape (512 tasks, random
+// values, CUDA events) and the faster one is used for the rest of the
+// process.  The decision is made the first time a bucket is seen.
+// ---------------------------------------------------------------------------
+namespace {
+int pow2_bucket(int v) {
+  int b = 16;
+  while (b < v && b < (1 << 20)) b <<= 1;
+  return b;
+}
+
+__global__ void fill_kernel(float* p, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    p[e] = (float)((e * 2654435761u) % 1000) * 1e-3f - 0.5f;
+}
+
+struct TuneKey {
+  int m, n, k;
+  bool operator<(const TuneKey& o) const {
+    return m != o.m ? m < o.m : (n != o.n ? n < o.n : k < o.k);
+  }
+};
+std::map<TuneKey, bool>& tune_table() {
+  static std::map<TuneKey, bool> t;
+  return t;
+}
+}  // namespace
+
+static bool autotune_use_tc(int maxM, int maxN, int ksum, cudaStream_t s) {
+  TuneKey key{pow2_bucket(maxM), pow2_bucket(maxN), pow2_bucket(ksum)};
+  auto& tab = tune_table();
+  auto it = tab.find(key);
+  if (it != tab.end()) return it->second;
+  const int M = key.m, N = key.n, K = std::min(key.k, 4096);
+  const int T = std::max(32, std::min(512, 131072 / K));
+  float *A = nullptr, *B = nullptr, *C = nullptr;
+  GemmTask* dt = nullptr;
+  GemmTerm* dm = nullptr;
+  bool tc = true;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  size_t na = (size_t)T * M * K, nb = (size_t)T * K * N, nc = (size_t)T * M * N;
+  if (cudaMalloc(&A, na * 4) == cudaSuccess && cudaMalloc(&B, nb * 4) == cudaSuccess &&
+      cudaMalloc(&C, nc * 4) == cudaSuccess && cudaMalloc(&dt, T * sizeof(GemmTask)) == cudaSuccess &&
+      cudaMalloc(&dm, T * sizeof(GemmTerm)) == cudaSuccess) {
+    std::vector<GemmTask> ht(T);
+    std::vector<GemmTerm> hm(T);
+    for (int t = 0; t < T; ++t) {
+      ht[t] = GemmTask{C + (size_t)t * M * N, nullptr, M, N, M, M, t, 1, 1.0, 0.0};
+      hm[t] = GemmTerm{A + (size_t)t * M * K, B + (size_t)t * K * N, K, M, K, 0};
+    }
+    fill_kernel<<<1024, 256, 0, s>>>(A, na);
+    fill_kernel<<<1024, 256, 0, s>>>(B, nb);
+    cudaMemcpyAsync(dt, ht.data(), T * sizeof(GemmTask), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dm, hm.data(), T * sizeof(GemmTerm), cudaMemcpyHostToDevice, s);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    launch_gemm_tc(dt, dm, T, M, N, s);   // warm both paths
+    gemm_kernel<float, false><<<dim3(T, tiles), NT, 0, s>>>(dt, dm);
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r) launch_gemm_tc(dt, dm, T, M, N, s);
+    cudaEventRecord(e1, s);
+    for (int r = 0; r < 3; ++r) gemm_kernel<float, false><<<dim3(T, tiles), NT, 0, s>>>(dt, dm);
+    cudaEventRecord(e2, s);
+    if (cudaEventSynchronize(e2) == cudaSuccess) {
+      float ttc = 0, tsimt = 0;
+      cudaEventElapsedTime(&ttc, e0, e1);
+      cudaEventElapsedTime(&tsimt, e1, e2);
+      tc = ttc <= tsimt;
+    }
+  }
+  (void)cudaGetLastError();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e2) cudaEventDestroy(e2);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(C);
+  cudaFree(dt);
+  cudaFree(dm);
+  tab[key] = tc;
+  return tc;
+}
+
+std::string autotune_report() {
+  std::string o = "[";
+  bool first = true;
+  for (auto& kv : tune_table()) {
+    o += (first ? "" : ",") + std::string("{\"m\":") + std::to_string(kv.first.m) + ",\"n\":" +
+         std::to_string(kv.first.n) + ",\"k\":" + std::to_string(kv.first.k) + ",\"kernel\":\"" +
+         (kv.second ? "tcgen05" : "simt") + "\"}";
+    first = false;
+  }
+  return o + "]";
 }
 
 void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
-                 int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64) {
+                 int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64, int ksum) {
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return;
   if (maxN <= GV_MAXN && !inputs_f64) {
     dim3 g(ntasks, (maxM + GV_ROWS - 1) / GV_ROWS);
@@ -263,7 +367,17 @@ void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
     H2_LAUNCH_CHECK();
     return;
   }
-  if (p == Prec::F32 && !inputs_f64 && tc_enabled() && maxM >= 32 && maxN >= 32) {
+  const int tm = tc_mode();
+  bool use_tc = false;
+  if (p == Prec::F32 && !inputs_f64 && maxM >= 32 && maxN >= 32 && tm != 0) {
+    if (tm == 1 || ksum <= 0) use_tc = true;
+    else {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(s, &cs);
+      use_tc = (cs != cudaStreamCaptureStatusNone) ? true : autotune_use_tc(maxM, maxN, ksum, s);
+    }
+  }
+  if (use_tc) {
     launch_gemm_tc(d_tasks, d_terms, ntasks, maxM, maxN, s);
     return;
   }
