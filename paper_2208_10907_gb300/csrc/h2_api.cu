@@ -1052,32 +1052,42 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   double* A = rt.LU->as<double>();
   int* piv = rt.piv->as<int>();
   int* info = (int*)sc.alloc(4, true);
+  // Blocked right-looking LU with pivoting inside each 64 x 64 diagonal
+  // block: the panel factorization touches only that block (one CTA, L2
+  // resident), and L21 = A21 U11^-1, U12 = L11^-1 A12 and the trailing
+  // update are batched over the whole width.  The factorization is exact
+  // (A = P L U, P a product of in-block row swaps).
   const int NB = 64;
+  double* Tbuf = (double*)sc.alloc((size_t)NB * n * 8);
+  std::vector<int> hp(NB);
   for (int k = 0; k < n; k += NB) {
     int nb = std::min(NB, n - k);
-    std::vector<LuTask> lt{LuTask{A + k + (size_t)k * n, n - k, nb, n, piv + k, info, spd ? 1 : 0}};
+    const int rest = n - k - nb;
+    std::vector<LuTask> lt{LuTask{A + k + (size_t)k * n, nb, nb, n, piv + k, info, spd ? 1 : 0}};
     run_getrf(Prec::F64, lt, sc);
-    // pivots are panel-relative: convert to global rows and apply to the
-    // columns left and right of the panel
-    std::vector<CopyTask> none;
-    // relative -> absolute pivots on the device via a tiny GEMM-free kernel:
-    // done on the host for simplicity (nb ints)
-    std::vector<int> hp(nb);
+    // block-relative pivots -> absolute rows, then swap the other columns
     H2_CUDA(cudaMemcpyAsync(hp.data(), piv + k, nb * 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaStreamSynchronize(s));
-    for (int& v : hp) v += k;
+    for (int q = 0; q < nb; ++q) hp[q] += k;
     H2_CUDA(cudaMemcpyAsync(piv + k, hp.data(), nb * 4, cudaMemcpyHostToDevice, s));
     launch_laswp_cols(Prec::F64, A, n, n, piv, k, k + nb, 0, k, s);
     launch_laswp_cols(Prec::F64, A, n, n, piv, k, k + nb, k + nb, n, s);
-    if (k + nb < n) {
+    if (rest > 0) {
       // U12 = L11^-1 A12
-      std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, A + k + (size_t)(k + nb) * n, nb, n - k - nb, n, n,
-                                        nullptr}};
-      run_trsm(Prec::F64, true, true, false, tt, n - k - nb, sc);
+      std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, A + k + (size_t)(k + nb) * n, nb, rest, n, n, nullptr}};
+      run_trsm(Prec::F64, true, true, false, tt, rest, sc);
+      // L21 = A21 U11^-1  via  U11^T L21^T = A21^T
+      double* A21 = A + (k + nb) + (size_t)k * n;
+      std::vector<CopyTask> c1{CopyTask{A21, Tbuf, nb, rest, n, nb}};
+      run_copy(Prec::F64, Prec::F64, true, c1, nb, rest, sc);
+      std::vector<TrsmTask> t2{TrsmTask{A + k + (size_t)k * n, Tbuf, nb, rest, n, nb, nullptr}};
+      run_trsm(Prec::F64, true, false, true, t2, rest, sc);
+      std::vector<CopyTask> c2{CopyTask{Tbuf, A21, rest, nb, nb, n}};
+      run_copy(Prec::F64, Prec::F64, true, c2, rest, nb, sc);
       // A22 -= L21 U12
       GemmBatch gb;
-      gb.add1(A + (k + nb) + (size_t)(k + nb) * n, n, n - k - nb, n - k - nb, A + (k + nb) + (size_t)k * n, n,
-              A + k + (size_t)(k + nb) * n, n, nb, -1.0, 1.0);
+      gb.add1(A + (k + nb) + (size_t)(k + nb) * n, n, rest, rest, A21, n, A + k + (size_t)(k + nb) * n, n, nb, -1.0,
+              1.0);
       gb.run(Prec::F64, false, false, sc);
     }
   }

@@ -29,10 +29,14 @@ __global__ void __launch_bounds__(NT) symv_pairs_kernel(const SymPairTask* __res
   __syncthreads();
   // warp w handles columns j = w, w + 8, ...; lane handles rows lane + 32 t
   T u[8][NR];
+  T xi[8][NR];   // this lane's rows of x_I, kept in registers for every column
 #pragma unroll
   for (int t = 0; t < 8; ++t)
 #pragma unroll
-    for (int c = 0; c < NR; ++c) u[t][c] = (T)0;
+    for (int c = 0; c < NR; ++c) {
+      u[t][c] = (T)0;
+      xi[t][c] = xI[lane + 32 * t][c];
+    }
   T* vout = reinterpret_cast<T*>(part) + tk.vo;
   // four columns per warp per pass: 32 independent loads per lane in flight
   for (int j0 = warp * 4; j0 < nJ; j0 += 32) {
@@ -53,13 +57,15 @@ __global__ void __launch_bounds__(NT) symv_pairs_kernel(const SymPairTask* __res
       T v[NR];
 #pragma unroll
       for (int c = 0; c < NR; ++c) v[c] = (T)0;
+      T xj[NR];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) xj[c] = (j < nJ) ? xJ[j][c] : (T)0;
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        int i = lane + 32 * t;
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
-          v[c] = fma(a[q][t], xI[i][c], v[c]);
-          u[t][c] = fma(a[q][t], (j < nJ) ? xJ[j][c] : (T)0, u[t][c]);
+          v[c] = fma(a[q][t], xi[t][c], v[c]);
+          u[t][c] = fma(a[q][t], xj[c], u[t][c]);
         }
       }
 #pragma unroll
