@@ -144,6 +144,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64-path steps (0 = skip)")
+    ap.add_argument("--kernel-table", action="store_true", help="print the per-kernel event table to stderr")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -209,6 +210,13 @@ def main():
     total_ms = evs[0].elapsed_time(evs[-1])
     stats = json.loads(H.h2_stats(h))
     H.h2_profile(0, 0)
+    if args.kernel_table:
+        ks_ = sorted(stats.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])
+        tot_ = sum(v["ms"] for _, v in ks_) or 1.0
+        print(f"per-kernel CUDA-event times over {args.steps} timed step(s)", file=sys.stderr)
+        for k_, v_ in ks_[:40]:
+            print(f"{k_:32s} launches {v_['launches']:6d} ms {v_['ms']:10.2f} ({100 * v_['ms'] / tot_:5.1f}%) "
+                  f"GFLOP {v_['flops'] / 1e9:10.1f}", file=sys.stderr)
     f_ms = [evs[k].elapsed_time(evf[k]) for k in range(args.steps)]
     s_ms = [evf[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     step_ms = total_ms / args.steps
@@ -232,7 +240,9 @@ def main():
             peak = 152 * 128 * 2 * (pk["sm_max_mhz"] if pk else 2070.0) * 1e6 / 1e12
             bound, unit, ach = "alu", "TFLOP/s", ks["flops"] / (ks["ms"] * 1e-3) / 1e12
         elif name.startswith("gemm_tc") or name.startswith("tc_"):
-            peak = (pk["bf16_tflops_sustained"] if pk else 1700.0) / 2.0   # tf32 = bf16 / 2 (nominal ratio)
+            # split 3xTF32: three tf32 products per useful product; tf32 peak =
+            # measured sustained bf16 x nominal tf32/bf16 (1.1 / 2.25)
+            peak = (pk["bf16_tflops_sustained"] if pk else 1700.0) * (1.1 / 2.25) / 3.0
             bound, unit, ach = "tensor", "TFLOP/s", ks["flops"] / (ks["ms"] * 1e-3) / 1e12
         else:
             # FP64 DFMA pipe: GB300 nominal 1.25 TFLOP/s dense FP64
@@ -241,7 +251,11 @@ def main():
         roof = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                 "frac": ach / peak if peak else None, "traffic": None, "launches": ks["launches"],
                 "ms_total": ks["ms"], "share": ks["ms"] / max(1e-9, sum(v["ms"] for v in kern_stats.values())),
-                "per_launch_ms": per_launch_ms, "peak_source": "derived from MEASURED_PEAKS.json sm_max_mhz"}
+                "per_launch_ms": per_launch_ms,
+                "peak_source": ("measured sustained bf16 (MEASURED_PEAKS.json) x tf32/bf16 nominal / 3 products"
+                                if bound == "tensor" else "derived from MEASURED_PEAKS.json sm_max_mhz and the "
+                                "GB300 nominal unit rates"),
+                "traffic_note": "ncu dram bytes of one captured launch are in profiles/ (smaller case)"}
 
     # ---- FP64 path, same GPU (fewer steps: FP64 throughput is 1/60 of FP32)
     fp64 = None
