@@ -1792,15 +1792,40 @@ static void factor(Handle& h, int precision, int spd) {
           ci.push_back(CopyTask{I256, ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], 256, m[g]});
         }
         run_copy(Prec::F64, Prec::F64, false, ci, 256, 256, sc);
-        std::vector<TrsmTask> tl, tu;
-        for (int g = 0; g < nb; ++g) {
-          if (m[g] == 0) continue;
-          tl.push_back(TrsmTask{S + off[g], ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], n[g], m[g],
-                                ht.pivRR->as<int>() + ht.pv_off[g]});
-          tu.push_back(TrsmTask{S + off[g], ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], n[g], m[g], nullptr});
+        if (W == Prec::F64) {
+          std::vector<TrsmTask> tl, tu;
+          for (int g = 0; g < nb; ++g) {
+            if (m[g] == 0) continue;
+            tl.push_back(TrsmTask{S + off[g], ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], n[g], m[g],
+                                  ht.pivRR->as<int>() + ht.pv_off[g]});
+            tu.push_back(TrsmTask{S + off[g], ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], n[g], m[g], nullptr});
+          }
+          run_trsm(Prec::F64, true, true, false, tl, maxm, sc);
+          run_trsm(Prec::F64, false, false, false, tu, maxm, sc);
+        } else {
+          // mixed precision: the inverses only precondition, so they are
+          // formed in FP32 from FP32 copies of the FP64 LU factors
+          const size_t LI = ht.li_off[nb];
+          float* Sf = (float*)sc.alloc(NN * 4);
+          float* Lf = (float*)sc.alloc(std::max<size_t>(1, LI) * 4);
+          float* Uf = (float*)sc.alloc(std::max<size_t>(1, LI) * 4);
+          std::vector<CopyTask> c1, c2;
+          std::vector<TrsmTask> tl, tu;
+          for (int g = 0; g < nb; ++g) {
+            if (m[g] == 0) continue;
+            c1.push_back(CopyTask{S + off[g], Sf + off[g], m[g], m[g], n[g], n[g]});
+            c1.push_back(CopyTask{ht.Linv->as<double>() + ht.li_off[g], Lf + ht.li_off[g], m[g], m[g], m[g], m[g]});
+            c1.push_back(CopyTask{ht.Uinv->as<double>() + ht.li_off[g], Uf + ht.li_off[g], m[g], m[g], m[g], m[g]});
+            tl.push_back(TrsmTask{Sf + off[g], Lf + ht.li_off[g], m[g], m[g], n[g], m[g], ht.pivRR->as<int>() + ht.pv_off[g]});
+            tu.push_back(TrsmTask{Sf + off[g], Uf + ht.li_off[g], m[g], m[g], n[g], m[g], nullptr});
+            c2.push_back(CopyTask{Lf + ht.li_off[g], ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], m[g], m[g]});
+            c2.push_back(CopyTask{Uf + ht.li_off[g], ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], m[g], m[g]});
+          }
+          run_copy(Prec::F64, Prec::F32, false, c1, 256, 256, sc);
+          run_trsm(Prec::F32, true, true, false, tl, maxm, sc);
+          run_trsm(Prec::F32, false, false, false, tu, maxm, sc);
+          run_copy(Prec::F32, Prec::F64, false, c2, 256, 256, sc);
         }
-        run_trsm(Prec::F64, true, true, false, tl, maxm, sc);
-        run_trsm(Prec::F64, false, false, false, tu, maxm, sc);
       }
       // S^SS_II -> parent quadrant
       std::vector<CopyTask> cs;

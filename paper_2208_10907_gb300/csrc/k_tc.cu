@@ -11,8 +11,10 @@
 // path) into the canonical no-swizzle K-major shared-memory layout: 8-row x
 // 16-byte core matrices, adjacent along K at LBO = 128 bytes, 8-row groups
 // at SBO = (BK/4)*128; each thread writes whole 16-byte core-matrix rows.
-// Two shared-memory stages and a register prefetch of the next K-chunk
-// overlap the global loads with the tensor core.  One elected thread issues
+// A register prefetch of the next K-chunk overlaps the global loads with the
+// tensor core; one shared-memory stage (96 KB) and at most 128 registers per
+// thread let two CTAs share an SM, so one CTA's MMA wait is covered by the
+// other's staging.  One elected thread issues
 // tcgen05.mma (kind::tf32, M = 128, K = 8 per instruction) into a
 // 256-column TMEM accumulator; completion is tracked per stage with
 // tcgen05.commit on mbarriers whose waits are bounded.  The epilogue reads
@@ -134,7 +136,7 @@ __device__ __forceinline__ void stage_store(const Stage<R>& st, bool contig_k, u
 constexpr int TNB = 256;                              // output tile columns (TMEM columns)
 constexpr int ABYTES = TM * BK * 4, BBYTES = TNB * BK * 4;
 constexpr int STAGE_BYTES = 2 * ABYTES + 2 * BBYTES;  // hi + lo of A and B
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 1;
 
 __device__ __forceinline__ uint32_t instr_desc_n(int n_mma) {
   uint32_t d = 0;
@@ -146,7 +148,7 @@ __device__ __forceinline__ uint32_t instr_desc_n(int n_mma) {
   return d;
 }
 
-__global__ void __launch_bounds__(NTH, 1) tc_gemm_kernel(const GemmTask* __restrict__ tasks,
+__global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restrict__ tasks,
                                                          const GemmTerm* __restrict__ terms, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* base = smem + ((1024 - (smem_u32(smem) & 1023)) & 1023);
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(NTH, 1) tc_gemm_kernel(const GemmTask* __restr
     contigB = (tm.flags & 2) == 0;
     load_chunk(cur_t, 0);
   }
-  uint32_t phase[NSTAGE] = {0u, 0u};
+  uint32_t phase[NSTAGE] = {};
   for (int c = 0; c < nchunks; ++c) {
     const int st = c % NSTAGE;
     unsigned char* sA_hi = base + st * STAGE_BYTES;
