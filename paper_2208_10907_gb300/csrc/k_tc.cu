@@ -81,10 +81,13 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 // Staging: an operand tile is R rows x BK k; its 16-byte units (one row, 4
 // consecutive k) are distributed so that each thread owns whole units and
-// writes them with one 16-byte shared store.  Two mappings: "row-fast"
-// (consecutive lanes take consecutive rows; global loads coalesce when the
-// operand is contiguous along rows) and "k-fast" (8 lanes cover one row's 32
-// k; loads coalesce when the operand is contiguous along k).
+// writes them with one 16-byte shared store.  A 16-byte store is served per
+// quarter warp, so every group of 8 consecutive lanes must write 8 different
+// rows of one core matrix (128 contiguous bytes) to be free of bank
+// conflicts.  Two mappings keep that property: "row-fast" (consecutive lanes
+// take consecutive rows; global loads coalesce when the operand is
+// contiguous along rows) and "k-fast" (a warp covers 8 rows x 16 k, each row
+// read as 64 contiguous bytes, for operands contiguous along k).
 template <int R>
 struct Stage {
   static constexpr int UNITS = R * (BK / 4);
@@ -92,19 +95,41 @@ struct Stage {
   float v[PER][4];
 };
 
+template <int R>
+__device__ __forceinline__ void unit_coords(int u, bool contig_k, int& row, int& kc) {
+  if (contig_k) {
+    const int w = u >> 5;                      // 32-unit group: 8 rows x 4 units of k
+    row = (u & 7) + 8 * (w >> 1);
+    kc = ((u >> 3) & 3) + 4 * (w & 1);
+  } else {
+    row = u % R;
+    kc = u / R;
+  }
+}
+
 // element (row, k) of op(X) with X column-major: rowmajor_k = true means
 // op(X)(row, k) = X[k + row*ld] (contiguous along k), else X[row + k*ld]
 template <int R>
 __device__ __forceinline__ void stage_load(Stage<R>& st, const float* X, long long ld, bool contig_k, int row0,
                                            int rows, int k0, int K) {
   const int tid = threadIdx.x;
+  // 16-byte vector loads along k when every unit start is 16-byte aligned
+  const bool vec = contig_k && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ld & 3) == 0) && ((k0 & 3) == 0);
 #pragma unroll
   for (int q = 0; q < Stage<R>::PER; ++q) {
     const int u = tid + q * NTH;
     int row, kc;
-    if (contig_k) { kc = u & 7; row = u >> 3; } else { row = u % R; kc = u / R; }
+    unit_coords<R>(u, contig_k, row, kc);
     const int gr = row0 + row;
     const int gk = k0 + kc * 4;
+    if (vec && gr < rows && gk + 3 < K) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(X + gk + (long long)gr * ld));
+      st.v[q][0] = t.x;
+      st.v[q][1] = t.y;
+      st.v[q][2] = t.z;
+      st.v[q][3] = t.w;
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       float v = 0.f;
@@ -121,7 +146,7 @@ __device__ __forceinline__ void stage_store(const Stage<R>& st, bool contig_k, u
   for (int q = 0; q < Stage<R>::PER; ++q) {
     const int u = tid + q * NTH;
     int row, kc;
-    if (contig_k) { kc = u & 7; row = u >> 3; } else { row = u % R; kc = u / R; }
+    unit_coords<R>(u, contig_k, row, kc);
     const uint32_t o = (uint32_t)((row & 7) * 16 + (row >> 3) * SBO + kc * 128);
     float4 h, l;
     h.x = tf32_hi(st.v[q][0]); l.x = st.v[q][0] - h.x;
