@@ -89,22 +89,63 @@ struct DBuf {
 };
 using DBufP = std::shared_ptr<DBuf>;
 
+// Stream-ordered scratch: everything lives until the Scratch is destroyed.
+// Task lists and small buffers are carved from 32 MB arenas (one device
+// allocation per arena instead of one per launch); large buffers get their
+// own allocation.
 struct Scratch {
+  static constexpr size_t ARENA = size_t(32) << 20, SMALL = size_t(1) << 20;
   std::vector<DBufP> bufs;
+  std::vector<uintptr_t> subs;   // validator entries of arena carvings
   cudaStream_t s;
+  DBufP arena;
+  size_t apos = 0;
   explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (uintptr_t k : subs) registry().erase(k);
+  }
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  void* carve(size_t bytes) {
+    const size_t b = (std::max<size_t>(bytes, 16) + 255) & ~size_t(255);
+    if (!arena || apos + b > arena->bytes) {
+      arena = std::make_shared<DBuf>(ARENA);
+      bufs.push_back(arena);
+      apos = 0;
+    }
+    void* p = (char*)arena->p + apos;
+    apos += b;
+    if (g_check) {
+      registry()[(uintptr_t)p] = bytes;
+      subs.push_back((uintptr_t)p);
+    }
+    return p;
+  }
   template <class T> T* up(const std::vector<T>& v) {
     if (v.empty()) return nullptr;
-    auto b = std::make_shared<DBuf>(v.size() * sizeof(T));
-    H2_CUDA(cudaMemcpyAsync(b->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-    bufs.push_back(b);
-    return b->template as<T>();
+    const size_t nb = v.size() * sizeof(T);
+    void* p;
+    if (nb <= SMALL) {
+      p = carve(nb);
+    } else {
+      auto b = std::make_shared<DBuf>(nb);
+      bufs.push_back(b);
+      p = b->p;
+    }
+    H2_CUDA(cudaMemcpyAsync(p, v.data(), nb, cudaMemcpyHostToDevice, s));
+    return reinterpret_cast<T*>(p);
   }
   void* alloc(size_t bytes, bool zero = false) {
-    auto b = std::make_shared<DBuf>(std::max<size_t>(bytes, 16));
-    if (zero) H2_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, s));
-    bufs.push_back(b);
-    return b->p;
+    void* p;
+    if (bytes <= SMALL) {
+      p = carve(bytes);
+    } else {
+      auto b = std::make_shared<DBuf>(bytes);
+      bufs.push_back(b);
+      p = b->p;
+    }
+    if (zero) H2_CUDA(cudaMemsetAsync(p, 0, std::max<size_t>(bytes, 16), s));
+    return p;
   }
 };
 
@@ -251,6 +292,42 @@ struct GemmBatch {
   }
 };
 
+
+// One (box, list position) pair with its scratch slot; the pairs of one
+// batched launch share a scratch buffer.
+struct PairSlot {
+  int g, k, j;       // box, position in its near/far list, partner box
+  size_t bytes, off; // slot size and offset in the chunk buffer
+};
+
+// The pairs (g, list[g][k]) accepted by `keep`, ordered by list position
+// and then by box, so that a chunk holds the same positions of every box.
+template <class Keep, class Bytes>
+static std::vector<PairSlot> near_pairs(const std::vector<std::vector<int>>& list, Keep keep, Bytes bytes) {
+  std::vector<PairSlot> v;
+  size_t maxdeg = 0;
+  for (const auto& l : list) maxdeg = std::max(maxdeg, l.size());
+  for (size_t k = 0; k < maxdeg; ++k)
+    for (int g = 0; g < (int)list.size(); ++g) {
+      if (k >= list[g].size()) continue;
+      const int j = list[g][k];
+      if (keep(g, j)) v.push_back(PairSlot{g, (int)k, j, bytes(g, j), 0});
+    }
+  return v;
+}
+
+// End of the chunk of pairs starting at p0 whose slots fit in `budget`
+// bytes (at least one pair); assigns the slot offsets.
+static size_t chunk_pairs(std::vector<PairSlot>& v, size_t p0, size_t budget) {
+  size_t tot = 0, p1 = p0;
+  for (; p1 < v.size(); ++p1) {
+    const size_t b = (v[p1].bytes + 255) & ~size_t(255);
+    if (p1 > p0 && tot + b > budget) break;
+    v[p1].off = tot;
+    tot += b;
+  }
+  return p1;
+}
 
 // Validate (H2_CHECK=1), upload and launch.
 static void run_trsm(Prec p, bool lower, bool unit, bool tr, const std::vector<TrsmTask>& v, int maxrhs, Scratch& sc) {
@@ -1266,6 +1343,22 @@ static void factor(Handle& h, int precision, int spd) {
     Height& ht = h.hs[H];
     Scratch sc(s);
     const int nb = ht.nb;
+    // scratch budget of the batched pair products (fill-in Gram, projection)
+    size_t pair_budget = size_t(256) << 20;
+    {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+        pair_budget = std::min<size_t>(size_t(4) << 30, std::max<size_t>(pair_budget, fr / 8));
+    }
+    void* pbuf = nullptr;
+    size_t pcap = 0;
+    auto pair_buf = [&](size_t need) -> void* {   // one buffer shared by the stream-ordered pair loops
+      if (need > pcap) {
+        pbuf = sc.alloc(need);
+        pcap = need;
+      }
+      return pbuf;
+    };
     std::vector<int>& n = ht.n;
     // n x n slots
     std::vector<size_t> off(nb + 1, 0);
@@ -1673,28 +1766,34 @@ static void factor(Handle& h, int precision, int spd) {
       g2.run(W, true, false, sc);
     }
     {
-      size_t maxdeg = 0;
-      for (int g = 0; g < nb; ++g) maxdeg = std::max(maxdeg, ht.near[g].size());
-      for (size_t k = 0; k < maxdeg; ++k) {
+      // near pairs: S^SS_IJ = U^S_I^T A_IJ U^S_J into the parent block, all
+      // pairs of a chunk in two launches (V = op(A_IJ) U^S_J, then U^S_I^T V)
+      std::vector<PairSlot> prs = near_pairs(
+          ht.near,
+          [&](int g, int j) {
+            int ld;
+            return j != g && dest(g, j, ld) != nullptr;   // skip mirrors of stored parent blocks
+          },
+          [&](int g, int j) { return (size_t)n[g] * r[j] * ws; });
+      for (size_t p0 = 0; p0 < prs.size();) {
+        const size_t p1 = chunk_pairs(prs, p0, pair_budget);
+        char* Vb = (char*)pair_buf(prs[p1 - 1].off + prs[p1 - 1].bytes);
         GemmBatch g1, g2;
-        for (int g = 0; g < nb; ++g) {
-          if (k >= ht.near[g].size()) continue;
-          int j = ht.near[g][k];
-          if (j == g) continue;
+        for (size_t q = p0; q < p1; ++q) {
+          const PairSlot& pr = prs[q];
+          const int g = pr.g, k = pr.k, j = pr.j;
           int ld;
           char* D = dest(g, j, ld);
-          if (!D) continue;                    // mirror of a stored parent block
-          char* V = (char*)Tmp + so[g] * ws;   // n_g x r_j
+          char* V = Vb + pr.off;                       // n_g x r_j
           g1.add1(V, n[g], n[g], r[j], Ablk[g][k].ptr, Ablk[g][k].ld, USp(j), n[j], n[j], 1.0, 0.0, nullptr, 0,
                   Ablk[g][k].tr ? 1 : 0);
           g2.add1(D, ld, r[g], r[j], USp(g), n[g], V, n[g], n[g]);
         }
         g1.run(W, false, false, sc);
         g2.run(W, true, false, sc);
+        p0 = p1;
       }
-      // far pairs at this level: W_I K(sk_I, sk_J) W_J^T
-      size_t maxfar = 0;
-      for (int g = 0; g < nb; ++g) maxfar = std::max(maxfar, ht.far[g].size());
+      // far pairs at this level: W_I K(sk_I, sk_J) W_J^T, chunked the same way
       std::vector<int> sk_all;
       std::vector<size_t> sko(nb + 1, 0);
       for (int g = 0; g < nb; ++g) {
@@ -1702,17 +1801,24 @@ static void factor(Handle& h, int precision, int spd) {
         sko[g + 1] = sk_all.size();
       }
       int* dsk = sc.up(sk_all);
-      for (size_t k = 0; k < maxfar; ++k) {
+      std::vector<PairSlot> fps = near_pairs(
+          ht.far,
+          [&](int g, int j) {
+            int ld;
+            return dest(g, j, ld) != nullptr;
+          },
+          [&](int g, int j) { return 2 * (size_t)r[g] * r[j] * ws; });
+      for (size_t p0 = 0; p0 < fps.size();) {
+        const size_t p1 = chunk_pairs(fps, p0, pair_budget);
+        char* Fb = (char*)pair_buf(fps[p1 - 1].off + fps[p1 - 1].bytes);
         std::vector<AsmTask> at;
         GemmBatch g1, g2;
         int maxc = 0;
-        for (int g = 0; g < nb; ++g) {
-          if (k >= ht.far[g].size()) continue;
-          int j = ht.far[g][k];
-          int ldd;
-          if (!dest(g, j, ldd)) continue;
-          char* Kb = (char*)Tmp + so[g] * ws;           // r_g x r_j
-          char* V = (char*)Mk + so[g] * ws;             // r_g x r_j
+        for (size_t q = p0; q < p1; ++q) {
+          const PairSlot& pr = fps[q];
+          const int g = pr.g, j = pr.j;
+          char* Kb = Fb + pr.off;                                 // r_g x r_j
+          char* V = Kb + (size_t)r[g] * r[j] * ws;                // r_g x r_j
           at.push_back(AsmTask{Kb, dsk + sko[g], dsk + sko[j], 0, 0, r[g], r[j], r[g]});
           maxc = std::max(maxc, r[j]);
           g1.add1(V, r[g], r[g], r[j], Wp(g), r[g], Kb, r[g], r[g]);
@@ -1723,6 +1829,7 @@ static void factor(Handle& h, int precision, int spd) {
         run_assemble(W, at, 256, maxc, pts, h.kp, sc);
         g1.run(W, false, false, sc);
         g2.run(W, false, true, sc);
+        p0 = p1;
       }
     }
     // ---------------- 4. partial LU of S^RR (eq. lu) -------------------

@@ -61,6 +61,18 @@ __device__ __forceinline__ float kernel_eval_f(const KParams& kp, double dx, dou
   return r2 == 0.0f ? v + (float)kp.nugget : v;
 }
 
+// FP32 throughout, for well-separated points only (far-field samples), whose
+// coordinate differences lose no relative accuracy to FP32 rounding
+__device__ __forceinline__ float kernel_eval_ff(const KParams& kp, float dx, float dy, float dz) {
+  float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  float r = sqrtf(r2);
+  if (kp.kind == 0) return 1.0f / (r + (float)kp.delta);
+  if (kp.kind == 1) return expf(-(float)kp.kappa * r) / (r + (float)kp.delta);
+  float s = 1.7320508f * r / (float)kp.ell;
+  float v = (1.0f + s) * expf(-s);
+  return r2 == 0.0f ? v + (float)kp.nugget : v;
+}
+
 template <typename T> struct KEval;
 template <> struct KEval<double> {
   static __device__ __forceinline__ double eval(const KParams& kp, double dx, double dy, double dz) {

@@ -556,6 +556,9 @@ __global__ void __launch_bounds__(NT) fold_kernel(const FoldTask* __restrict__ t
 // ---------------------------------------------------------------------------
 // G (+)= B B^T for B = K(x[cand], x[samp]), tiles 64 x 64, kernel values
 // generated on the fly (never stored).  Computed in T, accumulated in FP64.
+// In FP32 the coordinates are taken relative to the box's first candidate
+// (one FP64 subtraction per point and tile), so that the kernel evaluations
+// run on the FP32 pipes; the samples are far from the box.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(NT) kgram_kernel(const KgramTask* __restrict__ tasks, Points pts,
@@ -567,15 +570,27 @@ __global__ void __launch_bounds__(NT) kgram_kernel(const KgramTask* __restrict__
   __shared__ T As[16][68];
   __shared__ T Bs[16][68];
   __shared__ double ax[64], ay[64], az[64], bx[64], by[64], bz[64];
+  constexpr bool F32 = sizeof(T) == 4;
+  __shared__ float fa[3][64], fb[3][64], fs[3][16];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int g0 = tk.cand[0];
+  const double cx = pts.x[g0], cy = pts.y[g0], cz = pts.z[g0];
   if (tid < 64) {
     int i = i0 + tid;
     int g = i < tk.n ? tk.cand[i] : tk.cand[0];
     ax[tid] = pts.x[g]; ay[tid] = pts.y[g]; az[tid] = pts.z[g];
+    if (F32) {
+      fa[0][tid] = (float)(ax[tid] - cx); fa[1][tid] = (float)(ay[tid] - cy); fa[2][tid] = (float)(az[tid] - cz);
+    }
   } else if (tid < 128) {
     int j = j0 + tid - 64;
     int g = j < tk.n ? tk.cand[j] : tk.cand[0];
     bx[tid - 64] = pts.x[g]; by[tid - 64] = pts.y[g]; bz[tid - 64] = pts.z[g];
+    if (F32) {
+      fb[0][tid - 64] = (float)(bx[tid - 64] - cx);
+      fb[1][tid - 64] = (float)(by[tid - 64] - cy);
+      fb[2][tid - 64] = (float)(bz[tid - 64] - cz);
+    }
   }
   __syncthreads();
   T acc[4][4];
@@ -584,6 +599,15 @@ __global__ void __launch_bounds__(NT) kgram_kernel(const KgramTask* __restrict__
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
   for (int k0 = 0; k0 < tk.m; k0 += 16) {
+    if (F32) {
+      if (tid < 16 && k0 + tid < tk.m) {
+        const int g = tk.samp[k0 + tid];
+        fs[0][tid] = (float)(pts.x[g] - cx);
+        fs[1][tid] = (float)(pts.y[g] - cy);
+        fs[2][tid] = (float)(pts.z[g] - cz);
+      }
+      __syncthreads();
+    }
     {
       int i = tid % 64, kk = tid / 64;
 #pragma unroll
@@ -592,10 +616,16 @@ __global__ void __launch_bounds__(NT) kgram_kernel(const KgramTask* __restrict__
         int gk = k0 + k;
         T va = (T)0, vb = (T)0;
         if (gk < tk.m) {
-          int g = tk.samp[gk];
-          double sx = pts.x[g], sy = pts.y[g], sz = pts.z[g];
-          if (i0 + i < tk.n) va = KEval<T>::eval(kp, ax[i] - sx, ay[i] - sy, az[i] - sz);
-          if (j0 + i < tk.n) vb = KEval<T>::eval(kp, bx[i] - sx, by[i] - sy, bz[i] - sz);
+          if (F32) {
+            const float sx = fs[0][k], sy = fs[1][k], sz = fs[2][k];
+            if (i0 + i < tk.n) va = (T)kernel_eval_ff(kp, fa[0][i] - sx, fa[1][i] - sy, fa[2][i] - sz);
+            if (j0 + i < tk.n) vb = (T)kernel_eval_ff(kp, fb[0][i] - sx, fb[1][i] - sy, fb[2][i] - sz);
+          } else {
+            int g = tk.samp[gk];
+            double sx = pts.x[g], sy = pts.y[g], sz = pts.z[g];
+            if (i0 + i < tk.n) va = KEval<T>::eval(kp, ax[i] - sx, ay[i] - sy, az[i] - sz);
+            if (j0 + i < tk.n) vb = KEval<T>::eval(kp, bx[i] - sx, by[i] - sy, bz[i] - sz);
+          }
         }
         As[k][i] = va;
         Bs[k][i] = vb;
