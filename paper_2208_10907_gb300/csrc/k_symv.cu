@@ -92,6 +92,124 @@ __global__ void __launch_bounds__(NT) symv_pairs_kernel(const SymPairTask* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single right-hand side: the same pass in double-float arithmetic.  Each
+// FP64 block entry is split exactly by bit manipulation into a pair of FP32
+// values (hi = leading 24 significand bits, lo = the next 23), x likewise,
+// and every product a*x is formed as hi*hi (exact through an FMA residual)
+// plus the two cross terms, accumulated in an unnormalised (hi, lo) FP32
+// pair.  The relative error per product is about 2^-46; the work runs on the
+// FP32 pipes, which on this GPU are 64 times faster than FP64, so the pass
+// is bound by the HBM read of the blocks instead of by FP64 FMA throughput.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_split(double a, float& h, float& l) {
+  const unsigned hi32 = (unsigned)__double2hiint(a), lo32 = (unsigned)__double2loint(a);
+  const unsigned sign = hi32 & 0x80000000u;
+  const int fe = (int)((hi32 >> 20) & 0x7FFu) - 896;           // FP32 biased exponent of a
+  if (fe >= 24 && fe <= 254) {
+    const unsigned mh = (__funnelshift_l(lo32, hi32, 3)) & 0x7FFFFFu;   // significand bits 51..29
+    const unsigned ml = (lo32 >> 6) & 0x7FFFFFu;                       // significand bits 28..6
+    h = __uint_as_float(sign | ((unsigned)fe << 23) | mh);
+    const unsigned lb = sign | ((unsigned)(fe - 23) << 23);
+    l = __fsub_rn(__uint_as_float(lb | ml), __uint_as_float(lb));
+  } else if (((hi32 >> 20) & 0x7FFu) == 0u) {
+    h = 0.f;                                                  // zero or FP64 subnormal
+    l = 0.f;
+  } else {                                                    // outside the pair's range: round
+    h = __double2float_rn(a);
+    l = __double2float_rn(a - (double)h);
+  }
+}
+
+// (sh, sl) += (ah + al) * (xh + xl), dropping al*xl
+__device__ __forceinline__ void df_fma(float ah, float al, float xh, float xl, float& sh, float& sl) {
+  const float p = __fmul_rn(ah, xh);
+  const float pe = fmaf(ah, xh, -p);
+  const float c = fmaf(ah, xl, fmaf(al, xh, pe));
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sl = __fadd_rn(sl, __fadd_rn(e, c));
+  sh = s;
+}
+
+// (sh, sl) += (oh, ol)
+__device__ __forceinline__ void df_add(float oh, float ol, float& sh, float& sl) {
+  const float s = __fadd_rn(sh, oh);
+  const float bb = __fsub_rn(s, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(oh, bb));
+  sl = __fadd_rn(sl, __fadd_rn(e, ol));
+  sh = s;
+}
+
+__global__ void __launch_bounds__(NT) symv_pairs_df_kernel(const SymPairTask* __restrict__ tasks,
+                                                           const double* __restrict__ x, double* __restrict__ part) {
+  const SymPairTask tk = tasks[blockIdx.x];
+  const int nI = tk.nI, nJ = tk.nJ;
+  const double* A = reinterpret_cast<const double*>(tk.A);
+  __shared__ float xJh[256], xJl[256];
+  __shared__ double uacc[8][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    float h, l;
+    df_split(tid < nJ ? x[tk.sJ + tid] : 0.0, h, l);
+    xJh[tid] = h;
+    xJl[tid] = l;
+  }
+  float xih[8], xil[8], uh[8], ul[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int i = lane + 32 * t;
+    df_split(i < nI ? x[tk.sI + i] : 0.0, xih[t], xil[t]);
+    uh[t] = 0.f;
+    ul[t] = 0.f;
+  }
+  __syncthreads();
+  double* vout = part + tk.vo;
+  for (int j0 = warp * 4; j0 < nJ; j0 += 32) {
+    double a[4][8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q;
+      const double* col = A + (long long)min(j, nJ - 1) * tk.lda;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = lane + 32 * t;
+        a[q][t] = (i < nI && j < nJ) ? col[i] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q;
+      const float xjh = j < nJ ? xJh[j] : 0.f, xjl = j < nJ ? xJl[j] : 0.f;
+      float vh = 0.f, vl = 0.f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        float ah, al;
+        df_split(a[q][t], ah, al);
+        df_fma(ah, al, xih[t], xil[t], vh, vl);
+        df_fma(ah, al, xjh, xjl, uh[t], ul[t]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, vh, o), ol = __shfl_down_sync(0xffffffffu, vl, o);
+        df_add(oh, ol, vh, vl);
+      }
+      if (lane == 0 && j < nJ) vout[j] = (double)vh + (double)vl;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) uacc[warp][lane + 32 * t] = (double)uh[t] + (double)ul[t];
+  __syncthreads();
+  double* uout = part + tk.uo;
+  for (int i = tid; i < nI; i += NT) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += uacc[w][i];
+    uout[i] = s;
+  }
+}
+
 // y(box) = sum of its partials in list order.
 template <typename T>
 __global__ void __launch_bounds__(NT) gather_parts_kernel(const GatherTask* __restrict__ tasks, const long long* __restrict__ offs,
@@ -111,9 +229,14 @@ __global__ void __launch_bounds__(NT) gather_parts_kernel(const GatherTask* __re
 void launch_symv_pairs(const SymPairTask* d, int ntasks, const double* x, int64_t ldx, double* part, int nrhs,
                        cudaStream_t s) {
   if (ntasks <= 0) return;
+  if (nrhs == 1) {
+    ProfScope ps("symv_pairs_df", s);
+    symv_pairs_df_kernel<<<ntasks, NT, 0, s>>>(d, x, part);
+    H2_LAUNCH_CHECK();
+    return;
+  }
   ProfScope ps("symv_pairs_f64", s);
-  if (nrhs == 1) symv_pairs_kernel<double, 1><<<ntasks, NT, 0, s>>>(d, x, ldx, part);
-  else if (nrhs == 2) symv_pairs_kernel<double, 2><<<ntasks, NT, 0, s>>>(d, x, ldx, part);
+  if (nrhs == 2) symv_pairs_kernel<double, 2><<<ntasks, NT, 0, s>>>(d, x, ldx, part);
   else throw StatusError(1, "symv_pairs: nrhs > 2");
   H2_LAUNCH_CHECK();
 }

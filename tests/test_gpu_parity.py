@@ -57,6 +57,12 @@ def test_matvec_matches_oracle_operator(name):
         yo = op.matvec(xs)
         err = np.linalg.norm(yg - yo) / np.linalg.norm(yo)
         assert err < 1e-11, err
+        # one right-hand side takes the double-float near-field pass
+        x1 = torch.from_numpy(np.ascontiguousarray(xs[:, 0])).cuda()
+        y1 = torch.zeros_like(x1)
+        H.h2_matvec(h, x1, y1, 1, N)
+        err1 = np.linalg.norm(y1.cpu().numpy() - yo[:, 0]) / np.linalg.norm(yo[:, 0])
+        assert err1 < 1e-11, err1
     finally:
         H.h2_destroy(h)
 
