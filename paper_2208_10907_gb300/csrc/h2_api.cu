@@ -1120,13 +1120,18 @@ static PlanP build_matvec_plan(Handle& h, const double* x, double* y, int nrhs) 
 // ------------------------------------------------------------ root LU ----
 // Blocked right-looking LU with partial pivoting of the dense top-level
 // matrix (eq. BLR2final), then its inverse (the root solve becomes a GEMM).
-static void root_factor(Handle& h, Root& rt, int spd) {
+// Factor the top-level dense matrix in precision P (in place in `Aw`, n x n,
+// column-major): LU, log-determinant and the explicit inverse (FP64 in
+// rt.inv, FP64 copy of the factors in rt.LU).  Mixed precision runs it in
+// FP32 on the tensor-core GEMM: the root only preconditions there.
+static void root_factor(Handle& h, Root& rt, int spd, Prec P, void* Aw) {
   cudaStream_t s = h.s;
   const int n = rt.n;
   if (n == 0) return;
   if (n > 8192) throw StatusError(H2_ERR_ARG, "top-level dense matrix larger than 8192");
   Scratch sc(s);
-  double* A = rt.LU->as<double>();
+  const size_t es = esz(P);
+  auto at = [&](void* base, size_t i, size_t j) -> char* { return (char*)base + (i + j * (size_t)n) * es; };
   int* piv = rt.piv->as<int>();
   int* info = (int*)sc.alloc(4, true);
   // Blocked right-looking LU with pivoting inside each 64 x 64 diagonal
@@ -1135,37 +1140,36 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   // update are batched over the whole width.  The factorization is exact
   // (A = P L U, P a product of in-block row swaps).
   const int NB = 64;
-  double* Tbuf = (double*)sc.alloc((size_t)NB * n * 8);
+  void* Tbuf = sc.alloc((size_t)NB * n * es);
   std::vector<int> hp(NB);
   for (int k = 0; k < n; k += NB) {
     int nb = std::min(NB, n - k);
     const int rest = n - k - nb;
-    std::vector<LuTask> lt{LuTask{A + k + (size_t)k * n, nb, nb, n, piv + k, info, spd ? 1 : 0}};
-    run_getrf(Prec::F64, lt, sc);
+    std::vector<LuTask> lt{LuTask{at(Aw, k, k), nb, nb, n, piv + k, info, spd ? 1 : 0}};
+    run_getrf(P, lt, sc);
     // block-relative pivots -> absolute rows, then swap the other columns
     H2_CUDA(cudaMemcpyAsync(hp.data(), piv + k, nb * 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaStreamSynchronize(s));
     for (int q = 0; q < nb; ++q) hp[q] += k;
     H2_CUDA(cudaMemcpyAsync(piv + k, hp.data(), nb * 4, cudaMemcpyHostToDevice, s));
-    launch_laswp_cols(Prec::F64, A, n, n, piv, k, k + nb, 0, k, s);
-    launch_laswp_cols(Prec::F64, A, n, n, piv, k, k + nb, k + nb, n, s);
+    launch_laswp_cols(P, Aw, n, n, piv, k, k + nb, 0, k, s);
+    launch_laswp_cols(P, Aw, n, n, piv, k, k + nb, k + nb, n, s);
     if (rest > 0) {
       // U12 = L11^-1 A12
-      std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, A + k + (size_t)(k + nb) * n, nb, rest, n, n, nullptr}};
-      run_trsm(Prec::F64, true, true, false, tt, rest, sc);
+      std::vector<TrsmTask> tt{TrsmTask{at(Aw, k, k), at(Aw, k, k + nb), nb, rest, n, n, nullptr}};
+      run_trsm(P, true, true, false, tt, rest, sc);
       // L21 = A21 U11^-1  via  U11^T L21^T = A21^T
-      double* A21 = A + (k + nb) + (size_t)k * n;
+      void* A21 = at(Aw, k + nb, k);
       std::vector<CopyTask> c1{CopyTask{A21, Tbuf, nb, rest, n, nb}};
-      run_copy(Prec::F64, Prec::F64, true, c1, nb, rest, sc);
-      std::vector<TrsmTask> t2{TrsmTask{A + k + (size_t)k * n, Tbuf, nb, rest, n, nb, nullptr}};
-      run_trsm(Prec::F64, true, false, true, t2, rest, sc);
+      run_copy(P, P, true, c1, nb, rest, sc);
+      std::vector<TrsmTask> t2{TrsmTask{at(Aw, k, k), Tbuf, nb, rest, n, nb, nullptr}};
+      run_trsm(P, true, false, true, t2, rest, sc);
       std::vector<CopyTask> c2{CopyTask{Tbuf, A21, rest, nb, nb, n}};
-      run_copy(Prec::F64, Prec::F64, true, c2, rest, nb, sc);
+      run_copy(P, P, true, c2, rest, nb, sc);
       // A22 -= L21 U12
       GemmBatch gb;
-      gb.add1(A + (k + nb) + (size_t)(k + nb) * n, n, rest, rest, A21, n, A + k + (size_t)(k + nb) * n, n, nb, -1.0,
-              1.0);
-      gb.run(Prec::F64, false, false, sc);
+      gb.add1(at(Aw, k + nb, k + nb), n, rest, rest, A21, n, at(Aw, k, k + nb), n, nb, -1.0, 1.0);
+      gb.run(P, false, false, sc);
     }
   }
   int hinfo = 0;
@@ -1174,9 +1178,14 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   if (hinfo != 0)
     throw StatusError(spd ? H2_ERR_NOT_SPD : H2_ERR_SINGULAR,
                       spd ? "non-positive pivot in the top-level Cholesky" : "zero pivot in the top-level LU");
+  double* LU = rt.LU->as<double>();
+  if (P != Prec::F64) {
+    std::vector<CopyTask> ct{CopyTask{Aw, LU, n, n, n, n}};
+    run_copy(P, Prec::F64, false, ct, n, n, sc);
+  }
   // log-determinant
   {
-    std::vector<LuTask> lt{LuTask{A, n, n, n, piv, nullptr, 0}};
+    std::vector<LuTask> lt{LuTask{LU, n, n, n, piv, nullptr, 0}};
     double* o = (double*)sc.alloc(16);
     launch_logdet_lu(sc.up(lt), 1, o, o + 1, false, s);
     double ho[2];
@@ -1187,31 +1196,35 @@ static void root_factor(Handle& h, Root& rt, int spd) {
   }
   // inverse: X = U^-1 L^-1 P I, blocked by 256-row panels
   rt.inv = std::make_shared<DBuf>((size_t)n * n * 8);
-  double* X = rt.inv->as<double>();
-  launch_fill_eye(Prec::F64, X, n, n, s);
-  launch_laswp_cols(Prec::F64, X, n, n, piv, 0, n, 0, n, s);
+  void* X = (P == Prec::F64) ? rt.inv->p : sc.alloc((size_t)n * n * es);
+  launch_fill_eye(P, X, n, n, s);
+  launch_laswp_cols(P, X, n, n, piv, 0, n, 0, n, s);
   const int TB = 256;
   // forward: L (unit lower)
   for (int k = 0; k < n; k += TB) {
     int nb = std::min(TB, n - k);
-    std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, X + k, nb, n, n, n, nullptr}};
-    run_trsm(Prec::F64, true, true, false, tt, n, sc);
+    std::vector<TrsmTask> tt{TrsmTask{at(Aw, k, k), at(X, k, 0), nb, n, n, n, nullptr}};
+    run_trsm(P, true, true, false, tt, n, sc);
     if (k + nb < n) {
       GemmBatch gb;
-      gb.add1(X + k + nb, n, n - k - nb, n, A + (k + nb) + (size_t)k * n, n, X + k, n, nb, -1.0, 1.0);
-      gb.run(Prec::F64, false, false, sc);
+      gb.add1(at(X, k + nb, 0), n, n - k - nb, n, at(Aw, k + nb, k), n, at(X, k, 0), n, nb, -1.0, 1.0);
+      gb.run(P, false, false, sc);
     }
   }
   // backward: U (upper)
   for (int k = ((n - 1) / TB) * TB; k >= 0; k -= TB) {
     int nb = std::min(TB, n - k);
-    std::vector<TrsmTask> tt{TrsmTask{A + k + (size_t)k * n, X + k, nb, n, n, n, nullptr}};
-    run_trsm(Prec::F64, false, false, false, tt, n, sc);
+    std::vector<TrsmTask> tt{TrsmTask{at(Aw, k, k), at(X, k, 0), nb, n, n, n, nullptr}};
+    run_trsm(P, false, false, false, tt, n, sc);
     if (k > 0) {
       GemmBatch gb;
-      gb.add1(X, n, k, n, A + (size_t)k * n, n, X + k, n, nb, -1.0, 1.0);
-      gb.run(Prec::F64, false, false, sc);
+      gb.add1(X, n, k, n, at(Aw, 0, k), n, at(X, k, 0), n, nb, -1.0, 1.0);
+      gb.run(P, false, false, sc);
     }
+  }
+  if (P != Prec::F64) {
+    std::vector<CopyTask> ct{CopyTask{X, rt.inv->p, n, n, n, n}};
+    run_copy(P, Prec::F64, false, ct, n, n, sc);
   }
   H2_CUDA(cudaStreamSynchronize(s));
 }
@@ -1987,10 +2000,14 @@ static void factor(Handle& h, int precision, int spd) {
   for (auto& pb : h.probs) {
     Root& rt = pb.root;
     if (rt.n == 0) continue;
-    Scratch sc(s);
-    std::vector<CopyTask> ct{CopyTask{rt.A->p, rt.LU->p, rt.n, rt.n, rt.n, rt.n}};
-    run_copy(W, Prec::F64, false, ct, rt.n, rt.n, sc);
-    root_factor(h, rt, spd);
+    if (W == Prec::F64) {
+      Scratch sc(s);
+      std::vector<CopyTask> ct{CopyTask{rt.A->p, rt.LU->p, rt.n, rt.n, rt.n, rt.n}};
+      run_copy(W, Prec::F64, false, ct, rt.n, rt.n, sc);
+      root_factor(h, rt, spd, Prec::F64, rt.LU->p);
+    } else {
+      root_factor(h, rt, spd, W, rt.A->p);
+    }
     rt.A.reset();
   }
   prof_tag(nullptr);
