@@ -1463,6 +1463,33 @@ static void factor(Handle& h, int precision, int spd) {
       run_copy(W, W, false, ct, maxn, maxn, sc);
       run_getrf(W, lu, sc);
       ng.run(W, false, true, sc);
+    }
+    if (W == Prec::F32) {
+      // mixed precision: M_K = A_KK^-1 NG_K A_KK^-T through the explicit
+      // inverse A_KK^-1 = U^-1 L^-1 P (two triangular solves on the
+      // identity) and two tensor-core GEMMs
+      void* I256 = sc.alloc(256 * 256 * ws);
+      launch_fill_eye(W, I256, 256, 256, s);
+      std::vector<CopyTask> ci;
+      std::vector<TrsmTask> tl, tu;
+      GemmBatch x1, x2;
+      for (int g = 0; g < nb; ++g) {
+        if (!has_lu[g]) continue;
+        void* L = (char*)LUK + so[g] * ws;
+        void* Ai = (char*)Tmp + so[g] * ws;
+        void* M = (char*)Mk + so[g] * ws;
+        ci.push_back(CopyTask{I256, Ai, n[g], n[g], 256, n[g]});
+        tl.push_back(TrsmTask{L, Ai, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
+        tu.push_back(TrsmTask{L, Ai, n[g], n[g], n[g], n[g], nullptr});
+        x1.add1(L, n[g], n[g], n[g], Ai, n[g], M, n[g], n[g]);      // X = A^-1 NG (over the LU)
+        x2.add1(M, n[g], n[g], n[g], L, n[g], Ai, n[g], n[g]);      // M = X A^-T
+      }
+      run_copy(W, W, false, ci, maxn, maxn, sc);
+      run_trsm(W, true, true, false, tl, maxn, sc);
+      run_trsm(W, false, false, false, tu, maxn, sc);
+      x1.run(W, false, false, sc);
+      x2.run(W, false, true, sc);
+    } else {
       // M_K = A_KK^-1 NG_K A_KK^-T  (NG symmetric): X = A^-1 NG; M = A^-1 X^T
       std::vector<TrsmTask> tl, tu;
       std::vector<CopyTask> tr;
