@@ -120,8 +120,26 @@ __global__ void __launch_bounds__(NT) getrf_kernel(const LuTask* __restrict__ ta
     }
     for (int j = k + 1 + threadIdx.x; j < nc; j += NT) rowk[j] = A[k + (long long)j * lda];
     __syncthreads();
-    // trailing update, column by column, rows spread over the threads
-    for (int j = k + 1; j < nc; ++j) {
+    // trailing update, four columns at a time (their loads are issued
+    // together, so the L2 latency is paid once per four), rows spread over
+    // the threads
+    int j = k + 1;
+    for (; j + 3 < nc; j += 4) {
+      const T r0 = rowk[j], r1 = rowk[j + 1], r2 = rowk[j + 2], r3 = rowk[j + 3];
+      T* c0 = A + (long long)j * lda;
+      T* c1 = c0 + lda;
+      T* c2 = c1 + lda;
+      T* c3 = c2 + lda;
+      for (int i = k + 1 + threadIdx.x; i < m; i += NT) {
+        const T ci = colk[i];
+        const T v0 = c0[i], v1 = c1[i], v2 = c2[i], v3 = c3[i];
+        c0[i] = v0 - ci * r0;
+        c1[i] = v1 - ci * r1;
+        c2[i] = v2 - ci * r2;
+        c3[i] = v3 - ci * r3;
+      }
+    }
+    for (; j < nc; ++j) {
       const T rj = rowk[j];
       T* col = A + (long long)j * lda;
       for (int i = k + 1 + threadIdx.x; i < m; i += NT) col[i] -= colk[i] * rj;
@@ -180,7 +198,15 @@ __global__ void __launch_bounds__(NT) trsm_kernel(const TrsmTask* __restrict__ t
       }
       if (c < nc) {
         T xj = X[j * LDX + c];
-        for (int i = j + 1 + r0; i < n; i += RG) X[i * LDX + c] -= aij(i, j) * xj;
+        int i = j + 1 + r0;
+        for (; i + 3 * RG < n; i += 4 * RG) {   // four independent loads in flight
+          const T a0 = aij(i, j), a1 = aij(i + RG, j), a2 = aij(i + 2 * RG, j), a3 = aij(i + 3 * RG, j);
+          X[i * LDX + c] -= a0 * xj;
+          X[(i + RG) * LDX + c] -= a1 * xj;
+          X[(i + 2 * RG) * LDX + c] -= a2 * xj;
+          X[(i + 3 * RG) * LDX + c] -= a3 * xj;
+        }
+        for (; i < n; i += RG) X[i * LDX + c] -= aij(i, j) * xj;
       }
       __syncthreads();
     }
@@ -192,7 +218,15 @@ __global__ void __launch_bounds__(NT) trsm_kernel(const TrsmTask* __restrict__ t
       }
       if (c < nc) {
         T xj = X[j * LDX + c];
-        for (int i = r0; i < j; i += RG) X[i * LDX + c] -= aij(i, j) * xj;
+        int i = r0;
+        for (; i + 3 * RG < j; i += 4 * RG) {
+          const T a0 = aij(i, j), a1 = aij(i + RG, j), a2 = aij(i + 2 * RG, j), a3 = aij(i + 3 * RG, j);
+          X[i * LDX + c] -= a0 * xj;
+          X[(i + RG) * LDX + c] -= a1 * xj;
+          X[(i + 2 * RG) * LDX + c] -= a2 * xj;
+          X[(i + 3 * RG) * LDX + c] -= a3 * xj;
+        }
+        for (; i < j; i += RG) X[i * LDX + c] -= aij(i, j) * xj;
       }
       __syncthreads();
     }
@@ -280,13 +314,31 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
       rowk[j] = v;
     }
     __syncthreads();
+    // trailing update G -= r r^T, four columns at a time per thread (loads
+    // issued together), rows spread over the threads
     const int rem = n - k - 1;
-    const long long cnt = (long long)rem * rem;
-    for (long long e = threadIdx.x; e < cnt; e += NT) {
-      int i = k + 1 + (int)(e % rem);
-      int j = k + 1 + (int)(e / rem);
-      G[i + (long long)j * ld] -= rowk[i] * rowk[j];
+    for (int j0 = k + 1; j0 < n; j0 += 4) {
+      const int nj = min(4, n - j0);
+      double* g0 = G + (long long)j0 * ld;
+      if (nj == 4) {
+        const double r0 = rowk[j0], r1 = rowk[j0 + 1], r2 = rowk[j0 + 2], r3 = rowk[j0 + 3];
+        for (int i = k + 1 + threadIdx.x; i < n; i += NT) {
+          const double ri = rowk[i];
+          const double v0 = g0[i], v1 = g0[i + ld], v2 = g0[i + 2 * (long long)ld], v3 = g0[i + 3 * (long long)ld];
+          g0[i] = v0 - ri * r0;
+          g0[i + ld] = v1 - ri * r1;
+          g0[i + 2 * (long long)ld] = v2 - ri * r2;
+          g0[i + 3 * (long long)ld] = v3 - ri * r3;
+        }
+      } else {
+        for (int q = 0; q < nj; ++q) {
+          const double rj = rowk[j0 + q];
+          double* col = g0 + (long long)q * ld;
+          for (int i = k + 1 + threadIdx.x; i < n; i += NT) col[i] -= rowk[i] * rj;
+        }
+      }
     }
+    (void)rem;
     __syncthreads();
   }
   if (threadIdx.x == 0) *tk.rank = rank;
