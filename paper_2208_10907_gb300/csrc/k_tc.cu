@@ -17,7 +17,8 @@
 // other's staging.  One elected thread issues
 // tcgen05.mma (kind::tf32, M = 128, K = 8 per instruction) into a
 // 256-column TMEM accumulator; completion is tracked per stage with
-// tcgen05.commit on mbarriers whose waits are bounded.  The epilogue reads
+// tcgen05.commit on mbarriers, waited for (bounded) by one thread while the
+// others sleep in a CTA barrier.  The epilogue reads
 // TMEM with tcgen05.ld.32x32b.
 #include "h2_common.cuh"
 #include "h2_prof.h"
@@ -240,13 +241,14 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
     unsigned char* sB_hi = sA_lo + ABYTES;
     unsigned char* sB_lo = sB_hi + BBYTES;
     if (c >= NSTAGE) {
-      // the MMAs of chunk c - NSTAGE read this stage: wait for them (bounded)
-      bool ok = mbar_wait(&mbar[st], phase[st]);
-      phase[st] ^= 1u;
-      if (!ok && tid == 0) {
+      // the MMAs of chunk c - NSTAGE read this stage: one thread waits for
+      // them (bounded), the others sleep in the barrier instead of polling
+      if (tid == 0 && !s_fail && !mbar_wait(&mbar[st], phase[st])) {
         s_fail = 1;
         atomicExch(err, 1);
       }
+      phase[st] ^= 1u;
+      __syncthreads();
     }
     stage_store<TM>(ra, contigA, sA_hi, sA_lo);
     stage_store<TNB>(rb, contigB, sB_hi, sB_lo);
@@ -301,8 +303,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
   // wait for the last commit (it completes after every earlier MMA)
   if (nchunks > 0) {
     const int st = (nchunks - 1) % NSTAGE;
-    bool ok = mbar_wait(&mbar[st], phase[st]);
-    if (!ok && tid == 0) {
+    if (tid == 0 && !s_fail && !mbar_wait(&mbar[st], phase[st])) {
       s_fail = 1;
       atomicExch(err, 1);
     }
