@@ -1517,26 +1517,44 @@ static void factor(Handle& h, int precision, int spd) {
       // M = Tmp (symmetric up to rounding)
       std::swap(Mk, Tmp);
     }
-    // Gram of the fill-in block row: sum_K A_IK M_K A_IK^T, by near position
+    // Gram of the fill-in block row: sum_K A_IK M_K A_IK^T.  The products
+    // V_IK = op(A_IK) M_K of a chunk of near positions go in one launch; the
+    // sum over K is then accumulated into GF one near position at a time, so
+    // the FP32 summation order is the same for any chunking.
     void* GF = sc.alloc(so[nb] * ws, true);
     {
-      size_t maxdeg = 0;
-      for (int g = 0; g < nb; ++g) maxdeg = std::max(maxdeg, ht.near[g].size());
-      for (size_t k = 0; k < maxdeg; ++k) {
-        GemmBatch g1, g2;
-        for (int g = 0; g < nb; ++g) {
-          if (k >= ht.near[g].size()) continue;
-          int K = ht.near[g][k];
-          if (K == g || !has_lu[K]) continue;
-          void* V = (char*)Tmp + so[g] * ws;
-          int t = Ablk[g][k].tr;
-          g1.add1(V, n[g], n[g], n[K], Ablk[g][k].ptr, Ablk[g][k].ld, (char*)Mk + so[K] * ws, n[K], n[K], 1.0, 0.0,
-                  nullptr, 0, t ? 1 : 0);
-          g2.add1((char*)GF + so[g] * ws, n[g], n[g], n[g], V, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K], 1.0, 1.0,
-                  nullptr, 0, t ? 2 : 0);
+      std::vector<PairSlot> prs = near_pairs(ht.near, [&](int g, int K) { return K != g && has_lu[K]; },
+                                             [&](int g, int K) { return (size_t)n[g] * n[K] * ws; });
+      for (size_t p0 = 0; p0 < prs.size();) {
+        size_t p1 = chunk_pairs(prs, p0, pair_budget);
+        // end the chunk on a position boundary unless one position is too big
+        if (p1 < prs.size()) {
+          size_t q = p1;
+          while (q > p0 && prs[q - 1].k == prs[p1].k) --q;
+          if (q > p0) p1 = q;
+        }
+        char* Vb = (char*)pair_buf(prs[p1 - 1].off + prs[p1 - 1].bytes);
+        GemmBatch g1;
+        for (size_t q = p0; q < p1; ++q) {
+          const PairSlot& pr = prs[q];
+          const int g = pr.g, k = pr.k, K = pr.j;
+          g1.add1(Vb + pr.off, n[g], n[g], n[K], Ablk[g][k].ptr, Ablk[g][k].ld, (char*)Mk + so[K] * ws, n[K], n[K],
+                  1.0, 0.0, nullptr, 0, Ablk[g][k].tr ? 1 : 0);
         }
         g1.run(W, false, false, sc);
-        g2.run(W, false, true, sc);
+        for (size_t q0 = p0; q0 < p1;) {
+          size_t q1 = q0;
+          GemmBatch g2;
+          for (; q1 < p1 && prs[q1].k == prs[q0].k; ++q1) {
+            const PairSlot& pr = prs[q1];
+            const int g = pr.g, k = pr.k, K = pr.j;
+            g2.add1((char*)GF + so[g] * ws, n[g], n[g], n[g], Vb + pr.off, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K],
+                    1.0, 1.0, nullptr, 0, Ablk[g][k].tr ? 2 : 0);
+          }
+          g2.run(W, false, true, sc);
+          q0 = q1;
+        }
+        p0 = p1;
       }
     }
     // ---------------- 2. basis with fill-ins (eq. fillu) ---------------
