@@ -1517,43 +1517,47 @@ static void factor(Handle& h, int precision, int spd) {
       // M = Tmp (symmetric up to rounding)
       std::swap(Mk, Tmp);
     }
-    // Gram of the fill-in block row: sum_K A_IK M_K A_IK^T.  The products
-    // V_IK = op(A_IK) M_K of a chunk of near positions go in one launch; the
-    // sum over K is then accumulated into GF one near position at a time, so
-    // the FP32 summation order is the same for any chunking.
+    // Gram of the fill-in block row: sum_K A_IK M_K A_IK^T.  For a chunk of
+    // near positions, every pair's V_IK = op(A_IK) M_K and P_IK = V_IK A_IK^T
+    // go in one launch each; the P_IK are then added into GF one near
+    // position after the other, so the FP32 summation order does not depend
+    // on the chunking.
     void* GF = sc.alloc(so[nb] * ws, true);
     {
       std::vector<PairSlot> prs = near_pairs(ht.near, [&](int g, int K) { return K != g && has_lu[K]; },
-                                             [&](int g, int K) { return (size_t)n[g] * n[K] * ws; });
+                                             [&](int g, int K) { return ((size_t)n[g] * n[K] + (size_t)n[g] * n[g]) * ws; });
+      std::vector<std::vector<int>> by_box(nb);
       for (size_t p0 = 0; p0 < prs.size();) {
-        size_t p1 = chunk_pairs(prs, p0, pair_budget);
-        // end the chunk on a position boundary unless one position is too big
-        if (p1 < prs.size()) {
-          size_t q = p1;
-          while (q > p0 && prs[q - 1].k == prs[p1].k) --q;
-          if (q > p0) p1 = q;
-        }
+        const size_t p1 = chunk_pairs(prs, p0, pair_budget);
         char* Vb = (char*)pair_buf(prs[p1 - 1].off + prs[p1 - 1].bytes);
-        GemmBatch g1;
+        GemmBatch g1, g2;
         for (size_t q = p0; q < p1; ++q) {
           const PairSlot& pr = prs[q];
           const int g = pr.g, k = pr.k, K = pr.j;
-          g1.add1(Vb + pr.off, n[g], n[g], n[K], Ablk[g][k].ptr, Ablk[g][k].ld, (char*)Mk + so[K] * ws, n[K], n[K],
-                  1.0, 0.0, nullptr, 0, Ablk[g][k].tr ? 1 : 0);
+          char* V = Vb + pr.off;
+          char* P = V + (size_t)n[g] * n[K] * ws;
+          g1.add1(V, n[g], n[g], n[K], Ablk[g][k].ptr, Ablk[g][k].ld, (char*)Mk + so[K] * ws, n[K], n[K], 1.0, 0.0,
+                  nullptr, 0, Ablk[g][k].tr ? 1 : 0);
+          g2.add1(P, n[g], n[g], n[g], V, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K], 1.0, 0.0, nullptr, 0,
+                  Ablk[g][k].tr ? 2 : 0);
+          by_box[g].push_back((int)q);
         }
         g1.run(W, false, false, sc);
-        for (size_t q0 = p0; q0 < p1;) {
-          size_t q1 = q0;
-          GemmBatch g2;
-          for (; q1 < p1 && prs[q1].k == prs[q0].k; ++q1) {
-            const PairSlot& pr = prs[q1];
-            const int g = pr.g, k = pr.k, K = pr.j;
-            g2.add1((char*)GF + so[g] * ws, n[g], n[g], n[g], Vb + pr.off, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K],
-                    1.0, 1.0, nullptr, 0, Ablk[g][k].tr ? 2 : 0);
-          }
-          g2.run(W, false, true, sc);
-          q0 = q1;
+        prof_tag("fillin_gram");
+        g2.run(W, false, true, sc);
+        std::vector<AccumTask> at;
+        std::vector<const void*> parts;
+        long long maxe = 0;
+        for (int g = 0; g < nb; ++g) {
+          if (by_box[g].empty()) continue;
+          const long long ne = (long long)n[g] * n[g];
+          at.push_back(AccumTask{(char*)GF + so[g] * ws, ne, (int)parts.size(), (int)by_box[g].size()});
+          for (int q : by_box[g]) parts.push_back(Vb + prs[q].off + (size_t)n[g] * n[prs[q].j] * ws);
+          by_box[g].clear();
+          maxe = std::max(maxe, ne);
         }
+        launch_accum_parts(W, sc.up(at), (int)at.size(), sc.up(parts), maxe, s);
+        prof_tag("fillin");
         p0 = p1;
       }
     }

@@ -194,6 +194,12 @@ struct SymPairTask {   // stored block (I, J), I <= J: partials u (box I) and v 
   long long sI, sJ;    // tree-order starts of the boxes' rows in x
   long long uo, vo;    // element offsets of u (nI x nrhs) and v (nJ x nrhs) in the partial buffer
 };
+struct AccumTask {     // dst[0:n] += parts[p0], then += parts[p0+1], ... (in order)
+  void* dst;
+  long long n;
+  int p0, np;
+};
+
 struct GatherTask {    // y[s : s+n] = sum of partials p0 .. p0+np-1
   long long s;
   int n, p0, np;
@@ -240,6 +246,8 @@ void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int 
                        int col_begin, int col_end, cudaStream_t s);
 void launch_symv_pairs(const SymPairTask* d, int ntasks, const double* x, int64_t ldx, double* part, int nrhs,
                        cudaStream_t s);
+void launch_accum_parts(Prec p, const AccumTask* d, int ntasks, const void* const* parts, long long maxn,
+                        cudaStream_t s);
 void launch_gather_parts(const GatherTask* d, int ntasks, const long long* offs, const double* part, double* y,
                          int64_t ldy, int nrhs, cudaStream_t s);
 int tc_error_flag_read_and_clear(cudaStream_t s);

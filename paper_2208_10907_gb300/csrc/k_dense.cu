@@ -1093,6 +1093,29 @@ void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int 
   H2_LAUNCH_CHECK();
 }
 
+// dst += parts in list order, element by element (a fixed summation order)
+template <typename T>
+__global__ void __launch_bounds__(NT) accum_parts_kernel(const AccumTask* __restrict__ tasks,
+                                                         const void* const* __restrict__ parts) {
+  const AccumTask tk = tasks[blockIdx.x];
+  T* dst = reinterpret_cast<T*>(tk.dst);
+  for (long long e = (long long)blockIdx.y * NT + threadIdx.x; e < tk.n; e += (long long)gridDim.y * NT) {
+    T s = dst[e];
+    for (int q = tk.p0; q < tk.p0 + tk.np; ++q) s += reinterpret_cast<const T*>(parts[q])[e];
+    dst[e] = s;
+  }
+}
+
+void launch_accum_parts(Prec p, const AccumTask* d, int ntasks, const void* const* parts, long long maxn,
+                        cudaStream_t s) {
+  if (ntasks <= 0 || maxn <= 0) return;
+  ProfScope ps(p == Prec::F64 ? "accum_f64" : "accum_f32", s);
+  dim3 grid(ntasks, (unsigned)std::min<long long>(64, (maxn + NT - 1) / NT));
+  if (p == Prec::F64) accum_parts_kernel<double><<<grid, NT, 0, s>>>(d, parts);
+  else accum_parts_kernel<float><<<grid, NT, 0, s>>>(d, parts);
+  H2_LAUNCH_CHECK();
+}
+
 void launch_logdet_lu(const LuTask* d, int ntasks, double* out_log, double* out_sign, bool cholesky,
                       cudaStream_t s) {
   if (ntasks <= 0) return;
