@@ -1779,8 +1779,8 @@ static void factor(Handle& h, int precision, int spd) {
           if (pg <= qg) {
             Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[pg][q] * ws, lds[pg], 0});
           } else {
-            const auto& nl = up->near[qg];
-            size_t qq = std::find(nl.begin(), nl.end(), pg) - nl.begin();
+            const auto& nl = up->near[qg];   // sorted
+            size_t qq = std::lower_bound(nl.begin(), nl.end(), pg) - nl.begin();
             Anext[pg].push_back(PairRef{(char*)Anext_buf->p + po[qg][qq] * ws, lds[qg], 1});
           }
         }
@@ -1804,7 +1804,7 @@ static void factor(Handle& h, int precision, int spd) {
         int pj = ht.parent[j];
         if (pg > pj) return nullptr;
         const auto& nl = up->near[pg];
-        int q = (int)(std::find(nl.begin(), nl.end(), pj) - nl.begin());
+        int q = (int)(std::lower_bound(nl.begin(), nl.end(), pj) - nl.begin());   // near lists are sorted
         ld = Anext[pg][q].ld;
         return (char*)Anext[pg][q].ptr + ((size_t)rowoff + (size_t)coloff * ld) * ws;
       }
