@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <numeric>
 #include <sstream>
@@ -58,6 +59,8 @@ static size_t ext(long long r, long long c, long long ld) {
   return (size_t)((c - 1) * ld + r);
 }
 
+static bool scratch_cache_release();   // frees cached scratch; true if anything was held
+
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -68,6 +71,10 @@ struct DBuf {
     bytes = b;
     if (b) {
       cudaError_t e = cudaMalloc(&p, b);
+      if (e != cudaSuccess && scratch_cache_release()) {
+        (void)cudaGetLastError();
+        e = cudaMalloc(&p, b);
+      }
       if (e != cudaSuccess) {
         p = nullptr;
         (void)cudaGetLastError();
@@ -89,10 +96,59 @@ struct DBuf {
 };
 using DBufP = std::shared_ptr<DBuf>;
 
+// Device buffers of finished Scratch objects, kept for reuse by later ones
+// on the same stream: work on one stream runs in order, so a buffer handed
+// back after its last launch was queued can be handed out again at once.
+// Emptied when a device allocation fails and by h2_destroy.
+struct ScratchCache {
+  struct Entry {
+    DBufP b;
+    cudaStream_t s;
+  };
+  std::vector<Entry> v;
+  size_t total = 0;
+  std::mutex mu;
+  static constexpr size_t LIMIT = size_t(48) << 30;
+  DBufP take(size_t bytes, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(mu);
+    size_t best = v.size();
+    for (size_t i = 0; i < v.size(); ++i) {
+      const size_t b = v[i].b->bytes;
+      if (v[i].s != s || b < bytes || b > bytes + bytes / 4 + (size_t(64) << 20)) continue;
+      if (best == v.size() || b < v[best].b->bytes) best = i;
+    }
+    if (best == v.size()) return nullptr;
+    DBufP r = v[best].b;
+    total -= r->bytes;
+    v.erase(v.begin() + best);
+    return r;
+  }
+  void give(DBufP b, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!b || b.use_count() != 1 || total + b->bytes > LIMIT) return;
+    total += b->bytes;
+    v.push_back(Entry{std::move(b), s});
+  }
+};
+static ScratchCache& scratch_cache() {
+  static ScratchCache c;
+  return c;
+}
+static bool scratch_cache_release() {
+  ScratchCache& c = scratch_cache();
+  std::vector<ScratchCache::Entry> drop;
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    drop.swap(c.v);
+    c.total = 0;
+  }
+  return !drop.empty();   // the buffers are freed here
+}
+
 // Stream-ordered scratch: everything lives until the Scratch is destroyed.
 // Task lists and small buffers are carved from 32 MB arenas (one device
 // allocation per arena instead of one per launch); large buffers get their
-// own allocation.
+// own allocation.  Both come from, and go back to, the scratch cache.
 struct Scratch {
   static constexpr size_t ARENA = size_t(32) << 20, SMALL = size_t(1) << 20;
   std::vector<DBufP> bufs;
@@ -103,14 +159,21 @@ struct Scratch {
   explicit Scratch(cudaStream_t st) : s(st) {}
   ~Scratch() {
     for (uintptr_t k : subs) registry().erase(k);
+    arena.reset();
+    for (DBufP& b : bufs) scratch_cache().give(std::move(b), s);
+  }
+  DBufP fresh(size_t bytes) {
+    DBufP b = scratch_cache().take(bytes, s);
+    if (!b) b = std::make_shared<DBuf>(bytes);
+    bufs.push_back(b);
+    return b;
   }
   Scratch(const Scratch&) = delete;
   Scratch& operator=(const Scratch&) = delete;
   void* carve(size_t bytes) {
     const size_t b = (std::max<size_t>(bytes, 16) + 255) & ~size_t(255);
     if (!arena || apos + b > arena->bytes) {
-      arena = std::make_shared<DBuf>(ARENA);
-      bufs.push_back(arena);
+      arena = fresh(ARENA);
       apos = 0;
     }
     void* p = (char*)arena->p + apos;
@@ -125,25 +188,13 @@ struct Scratch {
     if (v.empty()) return nullptr;
     const size_t nb = v.size() * sizeof(T);
     void* p;
-    if (nb <= SMALL) {
-      p = carve(nb);
-    } else {
-      auto b = std::make_shared<DBuf>(nb);
-      bufs.push_back(b);
-      p = b->p;
-    }
+    p = nb <= SMALL ? carve(nb) : fresh(nb)->p;
     H2_CUDA(cudaMemcpyAsync(p, v.data(), nb, cudaMemcpyHostToDevice, s));
     return reinterpret_cast<T*>(p);
   }
   void* alloc(size_t bytes, bool zero = false) {
     void* p;
-    if (bytes <= SMALL) {
-      p = carve(bytes);
-    } else {
-      auto b = std::make_shared<DBuf>(bytes);
-      bufs.push_back(b);
-      p = b->p;
-    }
+    p = bytes <= SMALL ? carve(bytes) : fresh(bytes)->p;
     if (zero) H2_CUDA(cudaMemsetAsync(p, 0, std::max<size_t>(bytes, 16), s));
     return p;
   }
@@ -2860,6 +2911,9 @@ h2_status h2_profile(int32_t enable, int32_t reset) {
 
 const char* h2_last_error(void) { return g_err.c_str(); }
 
-void h2_destroy(h2_handle H) { delete H; }
+void h2_destroy(h2_handle H) {
+  delete H;
+  h2::scratch_cache_release();
+}
 
 }  // extern "C"
