@@ -145,6 +145,20 @@ static bool scratch_cache_release() {
   return !drop.empty();   // the buffers are freed here
 }
 
+// A buffer of at least `bytes` on stream s: the cached one if it fits, else
+// a new allocation.
+static DBufP cached_or_new(size_t bytes, cudaStream_t s) {
+  DBufP b = scratch_cache().take(bytes, s);
+  return b ? b : std::make_shared<DBuf>(bytes);
+}
+// Keep b when it is large enough (and not much larger) and nobody else holds
+// it; otherwise replace it.  Its contents are not preserved.
+static void ensure(DBufP& b, size_t bytes) {
+  if (b && b.use_count() == 1 && b->bytes >= bytes && b->bytes <= bytes + bytes / 4 + (size_t(64) << 20)) return;
+  b.reset();
+  b = std::make_shared<DBuf>(bytes);
+}
+
 // Stream-ordered scratch: everything lives until the Scratch is destroyed.
 // Task lists and small buffers are carved from 32 MB arenas (one device
 // allocation per arena instead of one per launch); large buffers get their
@@ -1365,7 +1379,7 @@ static void factor(Handle& h, int precision, int spd) {
     } else {
       // FP32 copy of the stored (i <= j) leaf near blocks for the mixed pass
       size_t tot = h.leaf_blk_off[h.leaf_pair_ptr[h.leaf_ref.size()]];
-      auto buf = std::make_shared<DBuf>(std::max<size_t>(1, tot) * 4);
+      auto buf = cached_or_new(std::max<size_t>(1, tot) * 4, s);
       Aown.push_back(buf);
       Scratch sc(s);
       std::vector<CopyTask> ct;
@@ -1733,10 +1747,10 @@ static void factor(Handle& h, int precision, int spd) {
     // orthogonalise: Q = [U^R U^S], W (r x r).  In mixed precision the
     // orthogonalisation runs in FP32 (Q and W only precondition there).
     ht.q_off = off;
-    ht.Q = std::make_shared<DBuf>(NN * 8);
+    ensure(ht.Q, NN * 8);
     ht.w_off.assign(nb + 1, 0);
     for (int g = 0; g < nb; ++g) ht.w_off[g + 1] = ht.w_off[g] + (size_t)r[g] * r[g];
-    ht.W = std::make_shared<DBuf>(std::max<size_t>(1, ht.w_off[nb]) * 8);
+    ensure(ht.W, std::max<size_t>(1, ht.w_off[nb]) * 8);
     if (W == Prec::F64) {
       double* V = (double*)sc.alloc(NN * 8);
       std::vector<HqrTask> qt;
@@ -1764,7 +1778,7 @@ static void factor(Handle& h, int precision, int spd) {
     const void* Qw = ht.Q->p;
     const void* Ww = ht.W->p;
     if (W == Prec::F32) {
-      ht.Qw = std::make_shared<DBuf>(NN * 4);
+      ensure(ht.Qw, NN * 4);
       auto Wf = std::make_shared<DBuf>(std::max<size_t>(1, ht.w_off[nb]) * 4);
       std::vector<CopyTask> ct, cw;
       for (int g = 0; g < nb; ++g) {
@@ -1820,7 +1834,7 @@ static void factor(Handle& h, int precision, int spd) {
         Apre.reset();
         if (h.opt.hbm_budget_bytes > 0 && (int64_t)(tot * ws) > h.opt.hbm_budget_bytes)
           throw StatusError(H2_ERR_BUDGET, "level near blocks need " + std::to_string(tot * ws) + " bytes");
-        Anext_buf = std::make_shared<DBuf>(std::max<size_t>(1, tot) * ws);
+        Anext_buf = cached_or_new(std::max<size_t>(1, tot) * ws, s);
         lds = up->n;
       }
       Anext.assign(up->nb, {});
@@ -1947,7 +1961,7 @@ static void factor(Handle& h, int precision, int spd) {
     }
     // ---------------- 4. partial LU of S^RR (eq. lu) -------------------
     prof_tag("elim");
-    ht.S = std::make_shared<DBuf>(NN * 8);
+    ensure(ht.S, NN * 8);
     {
       std::vector<CopyTask> ct;
       for (int g = 0; g < nb; ++g)
@@ -1960,8 +1974,8 @@ static void factor(Handle& h, int precision, int spd) {
       ht.pv_off[g + 1] = ht.pv_off[g] + m[g];
       ht.lt_off[g + 1] = ht.lt_off[g] + (size_t)m[g] * r[g];
     }
-    ht.pivRR = std::make_shared<DBuf>(std::max<size_t>(1, ht.pv_off[nb]) * 4);
-    ht.Lt = std::make_shared<DBuf>(std::max<size_t>(1, ht.lt_off[nb]) * 8);
+    ensure(ht.pivRR, std::max<size_t>(1, ht.pv_off[nb]) * 4);
+    ensure(ht.Lt, std::max<size_t>(1, ht.lt_off[nb]) * 8);
     int* info = (int*)sc.alloc(4, true);
     {
       double* S = ht.S->as<double>();
@@ -2000,8 +2014,8 @@ static void factor(Handle& h, int precision, int spd) {
       // them as products instead of sequential triangular solves
       ht.li_off.assign(nb + 1, 0);
       for (int g = 0; g < nb; ++g) ht.li_off[g + 1] = ht.li_off[g] + (size_t)m[g] * m[g];
-      ht.Linv = std::make_shared<DBuf>(std::max<size_t>(1, ht.li_off[nb]) * 8);
-      ht.Uinv = std::make_shared<DBuf>(std::max<size_t>(1, ht.li_off[nb]) * 8);
+      ensure(ht.Linv, std::max<size_t>(1, ht.li_off[nb]) * 8);
+      ensure(ht.Uinv, std::max<size_t>(1, ht.li_off[nb]) * 8);
       {
         double* I256 = (double*)sc.alloc(256 * 256 * 8);
         launch_fill_eye(Prec::F64, I256, 256, 256, s);
@@ -2067,7 +2081,7 @@ static void factor(Handle& h, int precision, int spd) {
     if (up) {
       std::vector<size_t> to(up->nb + 1, 0);
       for (int pg = 0; pg < up->nb; ++pg) to[pg + 1] = to[pg] + (size_t)up->n[pg] * up->n[pg];
-      auto Tn = std::make_shared<DBuf>(std::max<size_t>(1, to[up->nb]) * 8);
+      auto Tn = cached_or_new(std::max<size_t>(1, to[up->nb]) * 8, s);
       H2_CUDA(cudaMemsetAsync(Tn->p, 0, Tn->bytes, s));
       std::vector<CopyTask> ct;
       for (int g = 0; g < nb; ++g) {
@@ -2079,9 +2093,11 @@ static void factor(Handle& h, int precision, int spd) {
       }
       run_copy(Prec::F64, Prec::F64, false, ct, 256, 256, sc);
       H2_CUDA(cudaStreamSynchronize(s));
+      scratch_cache().give(std::move(Tcur), s);
       Tcur = Tn;
       t_off = to;
       Ablk = std::move(Anext);
+      for (DBufP& b : Aown) scratch_cache().give(std::move(b), s);
       Aown.clear();
       Aown.push_back(Anext_buf);
     }
