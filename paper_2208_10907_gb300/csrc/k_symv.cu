@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(NT) symv_pairs_kernel(const SymPairTask* __res
 // FP32 pipes, which on this GPU are 64 times faster than FP64, so the pass
 // is bound by the HBM read of the blocks instead of by FP64 FMA throughput.
 // ---------------------------------------------------------------------------
+constexpr int DFQ = 2;   // columns per warp pass of the double-float kernel
+
 __device__ __forceinline__ void df_split(double a, float& h, float& l) {
   const unsigned hi32 = (unsigned)__double2hiint(a), lo32 = (unsigned)__double2loint(a);
   const unsigned sign = hi32 & 0x80000000u;
@@ -142,7 +144,7 @@ __device__ __forceinline__ void df_add(float oh, float ol, float& sh, float& sl)
   sh = s;
 }
 
-__global__ void __launch_bounds__(NT) symv_pairs_df_kernel(const SymPairTask* __restrict__ tasks,
+__global__ void __launch_bounds__(NT, 3) symv_pairs_df_kernel(const SymPairTask* __restrict__ tasks,
                                                            const double* __restrict__ x, double* __restrict__ part) {
   const SymPairTask tk = tasks[blockIdx.x];
   const int nI = tk.nI, nJ = tk.nJ;
@@ -166,10 +168,11 @@ __global__ void __launch_bounds__(NT) symv_pairs_df_kernel(const SymPairTask* __
   }
   __syncthreads();
   double* vout = part + tk.vo;
-  for (int j0 = warp * 4; j0 < nJ; j0 += 32) {
-    double a[4][8];
+  // two columns per warp pass: few enough registers for three CTAs per SM
+  for (int j0 = warp * DFQ; j0 < nJ; j0 += 8 * DFQ) {
+    double a[DFQ][8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < DFQ; ++q) {
       const int j = j0 + q;
       const double* col = A + (long long)min(j, nJ - 1) * tk.lda;
 #pragma unroll
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(NT) symv_pairs_df_kernel(const SymPairTask* __
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < DFQ; ++q) {
       const int j = j0 + q;
       const float xjh = j < nJ ? xJh[j] : 0.f, xjl = j < nJ ? xJl[j] : 0.f;
       float vh = 0.f, vl = 0.f;
