@@ -451,6 +451,7 @@ struct Op {
   const double* x;      // kinds 3, 4
   double* y;
   long long ld;
+  double flops, bytes;  // algorithmic work of the launch (profiling counters)
 };
 
 struct Plan {
@@ -486,6 +487,8 @@ struct Plan {
     o.a = gb.maxM;
     o.b = gb.maxN;
     o.ld = gb.ksum;
+    o.flops = gb.flops;
+    o.bytes = gb.bytes * esz(p);
     o.tag = cur_tag;
     ops.push_back(o);
   }
@@ -530,6 +533,10 @@ struct Plan {
     o.y = part;
     o.ld = ldx;
     o.a = nrhs;
+    for (const SymPairTask& t : v) {   // every stored block read once, two products
+      o.bytes += 8.0 * t.nI * t.nJ;
+      o.flops += 4.0 * t.nI * t.nJ * nrhs;
+    }
     o.tag = cur_tag;
     ops.push_back(o);
   }
@@ -566,6 +573,7 @@ struct Plan {
   void issue(cudaStream_t st) const {
     for (const Op& o : ops) {
       prof_tag(o.tag);
+      if (o.flops > 0.0 || o.bytes > 0.0) prof_note(o.flops, o.bytes);
       if (o.kind == 0)
         launch_gemm(o.p, (const GemmTask*)o.tasks, (const GemmTerm*)o.terms, o.n, o.a, o.b, st, false, (int)o.ld);
       else if (o.kind == 1) launch_trsm(o.p, o.f1, o.f2, o.f3, (const TrsmTask*)o.tasks, o.n, o.a, st);

@@ -248,6 +248,9 @@ void launch_symv_pairs(const SymPairTask* d, int ntasks, const double* x, int64_
                        cudaStream_t s);
 void launch_accum_parts(Prec p, const AccumTask* d, int ntasks, const void* const* parts, long long maxn,
                         cudaStream_t s);
+// symv_pairs with one right-hand side writes (hi, lo) FP32 pairs into the
+// 8-byte partial slots, and gather_parts with one right-hand side reads them
+// that way; with two right-hand sides both use FP64 partials.
 void launch_gather_parts(const GatherTask* d, int ntasks, const long long* offs, const double* part, double* y,
                          int64_t ldy, int nrhs, cudaStream_t s);
 int tc_error_flag_read_and_clear(cudaStream_t s);

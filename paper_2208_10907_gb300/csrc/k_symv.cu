@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(NT, 3) symv_pairs_df_kernel(const SymPairTask*
   const int nI = tk.nI, nJ = tk.nJ;
   const double* A = reinterpret_cast<const double*>(tk.A);
   __shared__ float xJh[256], xJl[256];
-  __shared__ double uacc[8][256];
+  __shared__ float2 uacc[8][256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   {
     float h, l;
@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(NT, 3) symv_pairs_df_kernel(const SymPairTask*
     ul[t] = 0.f;
   }
   __syncthreads();
-  double* vout = part + tk.vo;
+  // partial results leave as unnormalised (hi, lo) FP32 pairs in the 8-byte
+  // slots of the partial buffer; the gather adds them in FP64
+  float2* vout = reinterpret_cast<float2*>(part) + tk.vo;
   // two columns per warp pass: few enough registers for three CTAs per SM
   for (int j0 = warp * DFQ; j0 < nJ; j0 += 8 * DFQ) {
     double a[DFQ][8];
@@ -198,23 +200,24 @@ __global__ void __launch_bounds__(NT, 3) symv_pairs_df_kernel(const SymPairTask*
         const float oh = __shfl_down_sync(0xffffffffu, vh, o), ol = __shfl_down_sync(0xffffffffu, vl, o);
         df_add(oh, ol, vh, vl);
       }
-      if (lane == 0 && j < nJ) vout[j] = (double)vh + (double)vl;
+      if (lane == 0 && j < nJ) vout[j] = make_float2(vh, vl);
     }
   }
 #pragma unroll
-  for (int t = 0; t < 8; ++t) uacc[warp][lane + 32 * t] = (double)uh[t] + (double)ul[t];
+  for (int t = 0; t < 8; ++t) uacc[warp][lane + 32 * t] = make_float2(uh[t], ul[t]);
   __syncthreads();
-  double* uout = part + tk.uo;
+  float2* uout = reinterpret_cast<float2*>(part) + tk.uo;
   for (int i = tid; i < nI; i += NT) {
-    double s = 0.0;
+    float sh = uacc[0][i].x, sl = uacc[0][i].y;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) s += uacc[w][i];
-    uout[i] = s;
+    for (int w = 1; w < 8; ++w) df_add(uacc[w][i].x, uacc[w][i].y, sh, sl);
+    uout[i] = make_float2(sh, sl);
   }
 }
 
-// y(box) = sum of its partials in list order.
-template <typename T>
+// y(box) = sum of its partials in list order (FP64 partials, or the
+// double-float kernel's (hi, lo) FP32 pairs when DF is set).
+template <typename T, bool DF>
 __global__ void __launch_bounds__(NT) gather_parts_kernel(const GatherTask* __restrict__ tasks, const long long* __restrict__ offs,
                                                           const T* __restrict__ part, T* __restrict__ y, long long ldy,
                                                           int nrhs) {
@@ -222,7 +225,15 @@ __global__ void __launch_bounds__(NT) gather_parts_kernel(const GatherTask* __re
   for (int e = threadIdx.x; e < tk.n * nrhs; e += NT) {
     int i = e % tk.n, c = e / tk.n;
     T s = (T)0;
-    for (int q = tk.p0; q < tk.p0 + tk.np; ++q) s += part[offs[q] + i + (long long)c * tk.n];
+    for (int q = tk.p0; q < tk.p0 + tk.np; ++q) {
+      const long long o = offs[q] + i + (long long)c * tk.n;
+      if (DF) {
+        const float2 v = reinterpret_cast<const float2*>(part)[o];
+        s += (T)v.x + (T)v.y;
+      } else {
+        s += part[o];
+      }
+    }
     y[tk.s + i + c * ldy] = s;
   }
 }
@@ -248,7 +259,9 @@ void launch_gather_parts(const GatherTask* d, int ntasks, const long long* offs,
                          int64_t ldy, int nrhs, cudaStream_t s) {
   if (ntasks <= 0) return;
   ProfScope ps("gather_parts_f64", s);
-  gather_parts_kernel<double><<<ntasks, NT, 0, s>>>(d, offs, part, y, ldy, nrhs);
+  // one right-hand side: the partials come from the double-float kernel
+  if (nrhs == 1) gather_parts_kernel<double, true><<<ntasks, NT, 0, s>>>(d, offs, part, y, ldy, nrhs);
+  else gather_parts_kernel<double, false><<<ntasks, NT, 0, s>>>(d, offs, part, y, ldy, nrhs);
   H2_LAUNCH_CHECK();
 }
 
