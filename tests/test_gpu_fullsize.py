@@ -1,0 +1,58 @@
+"""Full-size checks on the workload bench.py times: N = 2^20 points on the
+union of 16 ellipsoid and 16 torus surfaces, Laplace 1/(r + 1e-3), leaf 256,
+eta 1, tol 1e-6, sampled far field (16, 2), mixed-precision factor refined to
+an H^2 residual of 1e-10.  The oracle cannot factor this size, so the checks
+are properties that hold at any size, evaluated on sampled rows one by one
+with the oracle's FP64 kernel function: the H^2 matvec approximates the dense
+product, and the refined solution solves the dense system, both to the
+compression accuracy."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import h2ulv_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2208_10907_gb300 import h2ulv as H  # noqa: E402
+
+N = 1 << 20
+
+
+def dense_rows(X, rows, x):
+    """(K x)_i for the sampled rows i, one dense FP64 kernel row at a time."""
+    return np.array([O.kernel_matrix("laplace", X[i:i + 1], X)[0] @ x for i in rows])
+
+
+def test_bench_workload_matvec_and_solution_on_sampled_rows():
+    X = synth.surface_union(N, 4)
+    opt = H.make_options(eta=1.0, leaf=256, tol=1e-6, max_rank=128, far_s0=16, far_smin=2)
+    h = H.h2_construct(torch.from_numpy(X).cuda(), N, H.make_kernel("laplace"), opt)
+    try:
+        rows = np.sort(np.random.default_rng(77).choice(N, 48, replace=False))
+        # H^2 matvec (double-float near field) against dense rows
+        xs = synth.rhs(N, 1, 41)[:, 0].copy()
+        xt = torch.from_numpy(xs).cuda()
+        yt = torch.zeros_like(xt)
+        H.h2_matvec(h, xt, yt, 1, N)
+        yd = dense_rows(X, rows, xs)
+        err_mv = np.linalg.norm(yt.cpu().numpy()[rows] - yd) / np.linalg.norm(yd)
+        # refined mixed-precision solve, dense residual on the same rows
+        H.h2_factor(h, H.H2_MIXED)
+        b = synth.rhs(N, 1, 40)[:, 0].copy()
+        bt = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bt)
+        st, ach, it = H.h2_solve(h, bt, x, 1, N, 1e-10, 30)
+        assert st == H.H2_OK and ach[0] <= 1e-10, (st, ach, it)
+        r = b[rows] - dense_rows(X, rows, x.cpu().numpy())
+        err_res = np.linalg.norm(r) / np.linalg.norm(b[rows])
+        print(f"sampled-row matvec error {err_mv:.3e}, dense residual {err_res:.3e}, {it} iterations")
+        # measured 4.3e-7 and 2.1e-7 (tol 1e-6): bounds with a 10x margin
+        assert err_mv < 5e-6, err_mv
+        assert err_res < 5e-6, err_res
+    finally:
+        H.h2_destroy(h)

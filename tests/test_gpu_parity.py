@@ -23,6 +23,7 @@ CASES = {
     "ragged3000": (lambda: synth.sphere_ball(3000, 5), "laplace", 100, 1e-8, 64),
     "cube4k_dense": (lambda: synth.cube(4096, 0), "laplace", 256, 1e-8, 128),
     "tiny100": (lambda: synth.cube(100, 9), "laplace", 256, 1e-8, 128),
+    "cube4k_matern": (lambda: synth.cube(4096, 5), "matern32", 256, 1e-8, 128),
 }
 
 _cache = {}
@@ -126,12 +127,14 @@ def test_host_buffers_multiple_rhs():
         H.h2_destroy(h)
 
 
-def test_spd_path_matches_oracle_cholesky():
+@pytest.mark.parametrize("name", ["sphereball4k_yukawa", "cube4k_matern"])
+def test_spd_path_matches_oracle_cholesky(name):
     """spd = 1: redundant blocks and the root are factored without pivoting
     with positive pivots (the LDL^T form of the Cholesky-ULV); the log-det
-    equals the oracle's Cholesky factorization's."""
-    X, pb, op, fac = oracle_case("sphereball4k_yukawa")
-    _, kern, leaf, tol, mr = CASES["sphereball4k_yukawa"]
+    equals the oracle's Cholesky factorization's.  The Matern-3/2 case (plus
+    the nugget on the diagonal) is the covariance workload's kernel."""
+    X, pb, op, fac = oracle_case(name)
+    _, kern, leaf, tol, mr = CASES[name]
     facs = O.ULVFactor(pb, spd=True)
     N = len(X)
     b = synth.rhs(N, 1, 3)[:, 0].copy()
