@@ -1692,9 +1692,10 @@ static void factor(Handle& h, int precision, int spd) {
       // against the H^2 operator recovers the accuracy.
       const double tol_basis = (W == Prec::F32) ? std::max(h.opt.tol, 1.0 / 1024.0) : h.opt.tol;
       std::vector<CholTask> ct;
+      double* Lch = (double*)sc.alloc(NN * 8);
       for (int g = 0; g < nb; ++g)
         ct.push_back(CholTask{G + off[g], n[g], n[g], piv + (size_t)g * 256, R + off[g], rank + g, tol_basis,
-                              h.opt.max_rank, cinfo});
+                              h.opt.max_rank, cinfo, Lch + off[g]});
       run_pchol(ct, sc);
     }
     std::vector<int> hr(nb), hpiv((size_t)nb * 256);

@@ -124,7 +124,7 @@ struct TrsmTask {      // B <- op(A)^-1 B, A n x n triangular, B n x nrhs
   const int* piv;      // row interchanges applied to B first (getrs), or null
 };
 
-struct CholTask {      // pivoted Cholesky of an n x n Gram matrix (in place)
+struct CholTask {      // pivoted Cholesky of an n x n Gram matrix (G is read only)
   double* G;
   int n, ldg;
   int* piv;            // n
@@ -133,6 +133,7 @@ struct CholTask {      // pivoted Cholesky of an n x n Gram matrix (in place)
   double tol;
   int max_rank;
   int* info;           // set to 1 if a non-finite value is met (may be null)
+  double* L;           // n x n scratch (the factor column by column)
 };
 
 struct PqrTask {       // Householder QR with column pivoting of an m x n matrix

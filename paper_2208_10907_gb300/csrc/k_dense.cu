@@ -244,103 +244,97 @@ __global__ void __launch_bounds__(NT) trsm_kernel(const TrsmTask* __restrict__ t
 // when G_kk <= tol^2 G_11 (|R_kk| <= tol |R_11|) or at max_rank.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ tasks) {
+  // Left-looking: step k forms only column k of the factor, from G's pivot
+  // column and the k columns already computed (kept column-major in L so
+  // that their reads coalesce), and downdates the diagonal.  Stopping at
+  // rank r costs about n r^2 / 2 multiply-adds instead of the n^2 r of
+  // updating the whole trailing matrix.  Thread i owns position i (n <= 256).
   const CholTask tk = tasks[blockIdx.x];
-  double* G = tk.G;
+  const double* G = tk.G;
   const int n = tk.n, ld = tk.ldg;
-  double* R = tk.R;   // ld n
+  double* R = tk.R;    // ld n
+  double* L = tk.L;    // ld n: L(i, c) at L[i + c n], i in pivoted position order
   __shared__ double s_val[32];
   __shared__ int s_idx[32];
-  __shared__ double rowk[256];
-  for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) tk.piv[i] = i;
+  __shared__ double d[256];     // diagonal of the remaining Schur complement
+  __shared__ int perm[256];
+  __shared__ double lk[256];    // row k of L
+  const int i = threadIdx.x;
+  if (i < n) {
+    d[i] = G[i + (long long)i * ld];
+    perm[i] = i;
+  }
   __syncthreads();
   double d1 = 0.0;
   int rank = min(n, tk.max_rank);
   for (int k = 0; k < n; ++k) {
-    double best = -1.0;
+    double best = -INFINITY;
     int bi = 0x7fffffff;
-    for (int i = k + threadIdx.x; i < n; i += NT) {
-      double v = G[i + (long long)i * ld];
-      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    if (i >= k && i < n) {
+      best = d[i];
+      bi = i;
     }
     double pv;
     int p;
     block_argmax(best, bi, s_val, s_idx, pv, p);
-    if (p < k || p >= n) {   // NaN on the remaining diagonal: stop here, flag it
-      if (threadIdx.x == 0 && tk.info) *tk.info = 1;
+    if (p < k || p >= n || pv != pv || pv == INFINITY) {   // non-finite diagonal: stop, flag it
+      if (i == 0 && tk.info) *tk.info = 1;
+      rank = k;
+      break;
+    }
+    if (k == 0) d1 = pv;
+    if (k >= tk.max_rank || pv <= tk.tol * tk.tol * d1 || pv <= 0.0) {
       rank = k;
       break;
     }
     if (p != k) {
-      // symmetric swap of rows/cols k and p of the trailing matrix (full matrix)
-      for (int j = threadIdx.x; j < n; j += NT) {
-        double a = G[k + (long long)j * ld];
-        G[k + (long long)j * ld] = G[p + (long long)j * ld];
-        G[p + (long long)j * ld] = a;
+      if (i < k) {   // rows k and p of the computed columns
+        const double a = L[k + (long long)i * n];
+        L[k + (long long)i * n] = L[p + (long long)i * n];
+        L[p + (long long)i * n] = a;
       }
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += NT) {
-        double a = G[i + (long long)k * ld];
-        G[i + (long long)k * ld] = G[i + (long long)p * ld];
-        G[i + (long long)p * ld] = a;
-      }
-      for (int i = threadIdx.x; i < k; i += NT) {
-        double a = R[i + (long long)k * n];
-        R[i + (long long)k * n] = R[i + (long long)p * n];
-        R[i + (long long)p * n] = a;
-      }
-      if (threadIdx.x == 0) {
-        int t = tk.piv[k];
-        tk.piv[k] = tk.piv[p];
-        tk.piv[p] = t;
+      if (i == 0) {
+        const double t = d[k];
+        d[k] = d[p];
+        d[p] = t;
+        const int q = perm[k];
+        perm[k] = perm[p];
+        perm[p] = q;
       }
       __syncthreads();
     }
-    double gkk = G[k + (long long)k * ld];
-    if (gkk != gkk || fabs(gkk) == INFINITY) {
-      if (threadIdx.x == 0 && tk.info) *tk.info = 1;
-      rank = k;
-      break;
-    }
-    if (k == 0) d1 = gkk;
-    if (k >= tk.max_rank || gkk <= tk.tol * tk.tol * d1 || gkk <= 0.0) {
-      rank = k;
-      break;
-    }
-    double rkk = sqrt(gkk);
-    for (int j = k + threadIdx.x; j < n; j += NT) {
-      double v = (j == k) ? rkk : G[k + (long long)j * ld] / rkk;
-      R[k + (long long)j * n] = v;
-      rowk[j] = v;
-    }
+    if (i < k) lk[i] = L[k + (long long)i * n];
     __syncthreads();
-    // trailing update G -= r r^T, four columns at a time per thread (loads
-    // issued together), rows spread over the threads
-    const int rem = n - k - 1;
-    for (int j0 = k + 1; j0 < n; j0 += 4) {
-      const int nj = min(4, n - j0);
-      double* g0 = G + (long long)j0 * ld;
-      if (nj == 4) {
-        const double r0 = rowk[j0], r1 = rowk[j0 + 1], r2 = rowk[j0 + 2], r3 = rowk[j0 + 3];
-        for (int i = k + 1 + threadIdx.x; i < n; i += NT) {
-          const double ri = rowk[i];
-          const double v0 = g0[i], v1 = g0[i + ld], v2 = g0[i + 2 * (long long)ld], v3 = g0[i + 3 * (long long)ld];
-          g0[i] = v0 - ri * r0;
-          g0[i + ld] = v1 - ri * r1;
-          g0[i + 2 * (long long)ld] = v2 - ri * r2;
-          g0[i + 3 * (long long)ld] = v3 - ri * r3;
-        }
-      } else {
-        for (int q = 0; q < nj; ++q) {
-          const double rj = rowk[j0 + q];
-          double* col = g0 + (long long)q * ld;
-          for (int i = k + 1 + threadIdx.x; i < n; i += NT) col[i] -= rowk[i] * rj;
-        }
+    const double rkk = sqrt(d[k]);
+    if (i > k && i < n) {
+      const int pk = perm[k];
+      double c = G[perm[i] + (long long)pk * ld];
+      int q = 0;
+      double c1 = 0.0, c2 = 0.0, c3 = 0.0;
+      for (; q + 3 < k; q += 4) {   // four independent loads in flight
+        const double l0 = L[i + (long long)q * n], l1 = L[i + (long long)(q + 1) * n];
+        const double l2 = L[i + (long long)(q + 2) * n], l3 = L[i + (long long)(q + 3) * n];
+        c -= l0 * lk[q];
+        c1 -= l1 * lk[q + 1];
+        c2 -= l2 * lk[q + 2];
+        c3 -= l3 * lk[q + 3];
       }
+      for (; q < k; ++q) c -= L[i + (long long)q * n] * lk[q];
+      c += (c1 + c2) + c3;
+      const double v = c / rkk;
+      L[i + (long long)k * n] = v;
+      d[i] -= v * v;
+    } else if (i == k) {
+      L[k + (long long)k * n] = rkk;
     }
-    (void)rem;
     __syncthreads();
   }
+  // R = L^T (rows 0 .. rank-1), zero elsewhere; pivots in position order
+  for (int e = threadIdx.x; e < n * n; e += NT) {
+    const int c = e % n, j = e / n;   // R(c, j)
+    R[e] = (c < rank && c <= j) ? L[j + (long long)c * n] : 0.0;
+  }
+  if (i < n) tk.piv[i] = perm[i];
   if (threadIdx.x == 0) *tk.rank = rank;
 }
 
