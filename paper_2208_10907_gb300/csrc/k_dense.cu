@@ -476,13 +476,29 @@ __global__ void __launch_bounds__(NT) hqr_kernel(const HqrTask* __restrict__ tas
     }
     if (threadIdx.x == 0) s_beta = (vn2 > (T)0) ? beta : x0;
     __syncthreads();
-    for (int j = k + 1 + warp; j < r; j += nwarp) {
-      T sj = 0;
-      for (int i = k + lane; i < n; i += 32) sj += V[i + (long long)k * n] * M[i + (long long)j * n];
+    // reflector k applied to columns k+1 .. r-1, four columns per warp pass
+    // (the reflector entries are loaded once for the four)
+    for (int j0 = k + 1 + 4 * warp; j0 < r; j0 += 4 * nwarp) {
+      const int nj = min(4, r - j0);
+      T s[4] = {0, 0, 0, 0};
+      for (int i = k + lane; i < n; i += 32) {
+        const T v = V[i + (long long)k * n];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sj += __shfl_down_sync(0xffffffffu, sj, o);
-      sj = __shfl_sync(0xffffffffu, sj, 0);
-      for (int i = k + lane; i < n; i += 32) M[i + (long long)j * n] -= (T)2 * V[i + (long long)k * n] * sj;
+        for (int q = 0; q < 4; ++q)
+          if (q < nj) s[q] += v * M[i + (long long)(j0 + q) * n];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_down_sync(0xffffffffu, s[q], o);
+        s[q] = __shfl_sync(0xffffffffu, s[q], 0);
+      }
+      for (int i = k + lane; i < n; i += 32) {
+        const T v = (T)2 * V[i + (long long)k * n];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nj) M[i + (long long)(j0 + q) * n] -= v * s[q];
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) M[k + (long long)k * n] = s_beta;
@@ -502,16 +518,34 @@ __global__ void __launch_bounds__(NT) hqr_kernel(const HqrTask* __restrict__ tas
   }
   __syncthreads();
   for (int k = r - 1; k >= 0; --k) {
-    for (int c = warp; c < n; c += nwarp) {
-      int pos = c < r ? m + c : c - r;
-      T* q = Q + (long long)pos * n;
-      T sj = 0;
-      for (int i = k + lane; i < n; i += 32) sj += V[i + (long long)k * n] * q[i];
+    // H_k applied to every column, four columns per warp pass
+    for (int c0 = 4 * warp; c0 < n; c0 += 4 * nwarp) {
+      const int nc = min(4, n - c0);
+      T* qc[4];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sj += __shfl_down_sync(0xffffffffu, sj, o);
-      sj = __shfl_sync(0xffffffffu, sj, 0);
-      if (sj != (T)0)
-        for (int i = k + lane; i < n; i += 32) q[i] -= (T)2 * V[i + (long long)k * n] * sj;
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + min(q, nc - 1);
+        qc[q] = Q + (long long)(c < r ? m + c : c - r) * n;
+      }
+      T s[4] = {0, 0, 0, 0};
+      for (int i = k + lane; i < n; i += 32) {
+        const T v = V[i + (long long)k * n];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nc) s[q] += v * qc[q][i];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_down_sync(0xffffffffu, s[q], o);
+        s[q] = __shfl_sync(0xffffffffu, s[q], 0);
+      }
+      for (int i = k + lane; i < n; i += 32) {
+        const T v = (T)2 * V[i + (long long)k * n];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nc && s[q] != (T)0) qc[q][i] -= v * s[q];
+      }
     }
     __syncthreads();
   }
