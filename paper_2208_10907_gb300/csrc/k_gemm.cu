@@ -191,7 +191,29 @@ __global__ void __launch_bounds__(NT) gemv_kernel(const GemmTask* __restrict__ t
         T acc[GV_MAXN];
 #pragma unroll
         for (int c = 0; c < GV_MAXN; ++c) acc[c] = (T)0;
-        for (int k = lane; k < tm.K; k += 32) {
+        // four strided elements per lane per pass: their loads are issued
+        // together and feed independent accumulators
+        T acc2[GV_MAXN];
+#pragma unroll
+        for (int c = 0; c < GV_MAXN; ++c) acc2[c] = (T)0;
+        int k = lane;
+        for (; k + 96 < tm.K; k += 128) {
+          const T v0 = a[k], v1 = a[k + 32], v2 = a[k + 64], v3 = a[k + 96];
+          T x0[GV_MAXN], x1[GV_MAXN], x2[GV_MAXN], x3[GV_MAXN];
+          xload<T, NR>(x0, B, k, tm.ldb, TRB, tk.N);
+          xload<T, NR>(x1, B, k + 32, tm.ldb, TRB, tk.N);
+          xload<T, NR>(x2, B, k + 64, tm.ldb, TRB, tk.N);
+          xload<T, NR>(x3, B, k + 96, tm.ldb, TRB, tk.N);
+#pragma unroll
+          for (int c = 0; c < GV_MAXN; ++c)
+            if (c < NR) {
+              acc[c] = fma(v0, x0[c], acc[c]);
+              acc2[c] = fma(v1, x1[c], acc2[c]);
+              acc[c] = fma(v2, x2[c], acc[c]);
+              acc2[c] = fma(v3, x3[c], acc2[c]);
+            }
+        }
+        for (; k < tm.K; k += 32) {
           T v = a[k];
           T x0[GV_MAXN];
           xload<T, NR>(x0, B, k, tm.ldb, TRB, tk.N);
@@ -199,6 +221,8 @@ __global__ void __launch_bounds__(NT) gemv_kernel(const GemmTask* __restrict__ t
           for (int c = 0; c < GV_MAXN; ++c)
             if (c < NR) acc[c] = fma(v, x0[c], acc[c]);
         }
+#pragma unroll
+        for (int c = 0; c < GV_MAXN; ++c) acc[c] += acc2[c];
 #pragma unroll
         for (int c = 0; c < GV_MAXN; ++c) {
           if (c < NR) {
