@@ -388,6 +388,25 @@ def lu_logdet(lu, piv):
     return float(np.sum(np.log(np.abs(d)))), float(sign)
 
 
+def fill_in_terms(near_l, i):
+    """Sec. III-B (Fig. fill-in): the fill-ins of block row i are
+    A_{i,K} A_{K,K}^-1 A_{K,J} for every box K != i with a dense block to i
+    and every J != K with a dense block to K (reading O-5 A: J = i included).
+    Returns the (K, J) pairs, K in the order of i's near list, J in K's."""
+    return [(K, J) for K in near_l[i] if K != i for J in near_l[K] if J != K]
+
+
+def fill_in_blocks(near_l, i):
+    """Block positions that fill in in block row i and block column i: (i, J)
+    from the row terms and, by the symmetry of the near relation, (J, i) from
+    the column terms A_{J,K} A_{K,K}^-1 A_{K,i}."""
+    pos = set()
+    for K, J in fill_in_terms(near_l, i):
+        pos.add((i, J))
+        pos.add((J, i))
+    return sorted(pos)
+
+
 class ULVFactor:
     """The dependency-free H^2-ULV factorization.
 
@@ -450,11 +469,8 @@ class ULVFactor:
                     if len(fs) else np.zeros((n[I], 0))
                 Kn = [K for K in near[l][I] if K != I and K in lus]
                 if literal_fill:
-                    Fblocks = []
-                    for K in Kn:
-                        for J in near[l][K]:
-                            if J != K:
-                                Fblocks.append(A[(I, K)] @ sla.lu_solve(lus[K], A[(K, J)]))
+                    Fblocks = [A[(I, K)] @ sla.lu_solve(lus[K], A[(K, J)])
+                               for K, J in fill_in_terms(near[l], I) if K in lus]
                     F = np.hstack(Fblocks) if Fblocks else np.zeros((n[I], 0))
                     if T[I] is not None:
                         F = sla.solve(T[I], F)

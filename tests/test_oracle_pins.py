@@ -250,3 +250,16 @@ def test_spd_cholesky_path():
     xd = np.linalg.solve(A, b)
     assert rel[0] <= 1e-10
     assert F.logdet()[0] == pytest.approx(np.linalg.slogdet(A)[1], rel=1e-6)
+
+
+def test_fill_in_set_matches_paper_example():
+    """The paper's worked example of the fill-in pre-computation (fixture
+    tests/golden/fill_in_example.json, with its citation): eliminating the
+    other boxes of the first block row/column fills exactly A_{0,2}, A_{2,0}
+    and A_{0,0}.  Dropping the J = i terms (reading B) would miss A_{0,0};
+    counting K = i would add the dense blocks themselves."""
+    import json
+    import os
+    fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fill_in_example.json")))
+    got = O.fill_in_blocks(fx["near"], fx["row"])
+    assert [list(p) for p in got] == fx["fill_in"]
