@@ -144,7 +144,10 @@ h2_status h2_solve(h2_handle h, const double* b, double* x, int32_t nrhs, int64_
 
 /* y = A_H2 x, the H^2 operator used as the refinement residual (near blocks
  * exact, far blocks through the nested bases, eq. transfer).
- *   x, y : N x nrhs column-major, leading dimension ld (host or device) */
+ *   x, y : N x nrhs column-major, leading dimension ld (host or device)
+ * With nrhs = 1 the near-field products run in double-float arithmetic
+ * (FP64 entries split exactly into FP32 pairs; about 2^-46 relative per
+ * product); the far field and all sums are FP64. */
 h2_status h2_matvec(h2_handle h, const double* x, double* y, int32_t nrhs, int64_t ld);
 
 /* log|det A| and its sign from the factorization: the sum over every level
@@ -235,7 +238,9 @@ h2_status h2_set_rank_predictor(h2_handle h, h2_mlp m, double margin);
 /* Thread-local message of the last failed call on this thread. */
 const char* h2_last_error(void);
 
-/* Free every device buffer owned by the handle. */
+/* Free every device buffer owned by the handle, and the library's cache of
+ * released scratch buffers (kept between calls for reuse on the same
+ * stream). */
 void h2_destroy(h2_handle h);
 
 #ifdef __cplusplus
