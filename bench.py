@@ -109,6 +109,27 @@ def cpu_oracle_sample(n_sample, repeats=1):
                        f"to N=2^20 (O(N) method); construct {np.median([t[0] for t in ts]):.2f} s not included")
 
 
+def dist_init(world):
+    """One process per GPU over NCCL; gloo when CUDA is absent (CPU tests of
+    the multi-rank path).  Replicas: no collective touches the data path,
+    only the barrier and the max over ranks of the step time."""
+    import torch
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return dist
+
+
+def max_over_ranks(x, world, device=None):
+    """The largest value of x over all ranks (the step time of the job)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -156,8 +177,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    dist_init(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     W = WORKLOAD
@@ -221,11 +241,7 @@ def main():
     s_ms = [evf[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     step_ms = total_ms / args.steps
     solve_ms = float(np.mean(s_ms))
-    # max over ranks
-    t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, world, dev)
 
     # ---- roofline of the dominant kernel (event times inside the timed region)
     kern_stats = stats.get("kernels", {})
