@@ -152,3 +152,27 @@ def test_spd_path_matches_oracle_cholesky(name):
         assert np.linalg.norm(xt.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
     finally:
         H.h2_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [H.H2_FP64, H.H2_MIXED])
+def test_64_right_hand_sides(precision):
+    """64 right-hand sides (the Yukawa workload's block solve): more than 8
+    columns take the stationary refinement x <- x + ULV^-1 (b - A_H2 x)
+    column block at once; every column reaches the target and matches the
+    oracle's refined solution."""
+    X, pb, op, fac = oracle_case("sphereball4k_yukawa")
+    _, kern, leaf, tol, mr = CASES["sphereball4k_yukawa"]
+    N = len(X)
+    B = synth.rhs(N, 64, 12)
+    h = gpu_handle(X, kern, leaf, tol, mr)
+    try:
+        H.h2_factor(h, precision)
+        bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+        xt = torch.zeros_like(bt)
+        st, ach, it = H.h2_solve(h, bt, xt, 64, N, 1e-10, 40)
+        assert st == H.H2_OK and np.all(ach <= 1e-10), (st, ach.max(), it)
+        xo, _, _ = O.refine(op, fac, B, 1e-10, 30)
+        err = np.linalg.norm(xt.cpu().numpy().T - xo) / np.linalg.norm(xo)
+        assert err <= 1e-8, err
+    finally:
+        H.h2_destroy(h)
