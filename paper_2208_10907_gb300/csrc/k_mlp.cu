@@ -13,8 +13,6 @@ namespace {
 constexpr int NT = 256;
 constexpr int WID = MLP_WIDTH;
 
-__device__ __forceinline__ int p_W1() { return 0; }
-
 struct Off {
   int W1, b1, W2, b2, w3, b3, P;
   __host__ __device__ explicit Off(int F) {
