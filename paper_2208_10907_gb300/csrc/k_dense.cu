@@ -351,7 +351,6 @@ __global__ void __launch_bounds__(NT) pqr_kernel(const PqrTask* __restrict__ tas
   __shared__ double s_val[32];
   __shared__ int s_idx[32];
   __shared__ double nrm[256];
-  __shared__ double wv[256];
   __shared__ double s_beta, s_r11;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = NT / 32;
   for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
@@ -437,7 +436,6 @@ __global__ void __launch_bounds__(NT) pqr_kernel(const PqrTask* __restrict__ tas
     for (int j = k + 1 + threadIdx.x; j < n; j += NT) R[k + (long long)j * n] = A[k + (long long)j * lda];
     __syncthreads();
   }
-  (void)wv;
   if (threadIdx.x == 0) *tk.rank = rank;
 }
 
