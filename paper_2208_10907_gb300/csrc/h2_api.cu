@@ -933,7 +933,6 @@ static void build_operator(Handle& h) {
     }
     int* d_samp = sc.up(samp_all);
     int* d_cand = sc.up(cand_all);
-    size_t rtot = 0;
     std::vector<size_t> r_off(ht.nb + 1, 0);
     for (int g = 0; g < ht.nb; ++g) r_off[g + 1] = r_off[g] + (size_t)ht.n_op[g] * ht.n_op[g];
     double* R0 = (double*)sc.alloc(r_off[ht.nb] * 8, true);
