@@ -11,10 +11,10 @@ geometry with the Yukawa kernel (Section V).  The paper's hemoglobin BEM
 mesh is not available, so a union of ellipsoid and torus surfaces replaces
 it.
 """
-from .points import (cube, sphere_ball, surface_union, batched_problems,
+from .points import (cube, line, sphere_ball, surface_union, batched_problems,
                      cube_surface, sphere_surface, ellipsoid_surface, rhs,
                      workload)
 
-__all__ = ["cube", "sphere_ball", "surface_union", "batched_problems",
+__all__ = ["cube", "line", "sphere_ball", "surface_union", "batched_problems",
            "cube_surface", "sphere_surface", "ellipsoid_surface", "rhs",
            "workload"]

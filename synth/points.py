@@ -16,6 +16,13 @@ def sphere_surface(n, rng):
     return _unit_vectors(rng, n)
 
 
+def line(n, seed):
+    """n points uniform on the segment [0,1] x {0} x {0}, sorted (1-D
+    geometry, where weak admissibility gives the HSS structure)."""
+    x = np.sort(np.random.default_rng(seed).random(n))
+    return np.stack([x, np.zeros(n), np.zeros(n)], 1)
+
+
 def sphere_ball(n, seed):
     """Half the points uniform on the unit sphere, half uniform in the ball."""
     rng = np.random.default_rng(seed)

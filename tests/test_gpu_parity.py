@@ -176,3 +176,40 @@ def test_64_right_hand_sides(precision):
         assert err <= 1e-8, err
     finally:
         H.h2_destroy(h)
+
+
+def test_hss_special_case_weak_admissibility():
+    """eta -> infinity on a line: distinct boxes are far from the first level
+    below the root on (weak admissibility), there are no fill-ins, and the
+    method reduces to the paper's HSS-ULV (Sec. II-C).  Exact far-field block
+    rows (far_s0 = 0).  The FP64 refined solution matches the oracle's.  The
+    log-det is that of the factored approximation: its basis comes from the
+    Gram matrix B B^T, whose pivoted Cholesky resolves the block row only to
+    about sqrt(eps) = 1.5e-8 of its norm (below tol = 1e-10 here), so the
+    factored matrix is within about 3e-8 ||A|| of A and
+    |log det - log det A| <= N cond(A) 3e-8 against the dense log-det (the
+    oracle's own value moves by 1e-2 between CPU platforms for this case)."""
+    X = synth.line(1024, 5)
+    N = len(X)
+    pb = O.Problem(X, "laplace", 64, 1e12, 1e-10, 128, s0=0)
+    assert all(pb.near[pb.L][i] == [i] for i in range(2 ** pb.L))
+    op, fac = O.H2Operator(pb), O.ULVFactor(pb)
+    b = synth.rhs(N, 1, 9)[:, 0].copy()
+    xo, _, _ = O.refine(op, fac, b, 1e-10, 30)
+    pts = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    h = H.h2_construct(pts, N, H.make_kernel("laplace"),
+                       H.make_options(eta=1e12, leaf=64, tol=1e-10, max_rank=128, far_s0=0, far_smin=1))
+    try:
+        H.h2_factor(h, H.H2_FP64)
+        bt = torch.from_numpy(b).cuda()
+        xt = torch.zeros_like(bt)
+        st, ach, it = H.h2_solve(h, bt, xt, 1, N, 1e-10, 30)
+        assert st == H.H2_OK and ach[0] <= 1e-10, (st, ach, it)
+        assert np.linalg.norm(xt.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
+        ld, sg = H.h2_logdet(h)
+        A = O.kernel_matrix("laplace", X, X)
+        so, lo = np.linalg.slogdet(A)
+        bound = N * np.linalg.cond(A) * 3e-8
+        assert sg[0] == so and abs(ld[0] - lo) <= bound, (ld[0], lo, bound)
+    finally:
+        H.h2_destroy(h)
