@@ -9,7 +9,7 @@ use is ``synth`` (seeded inputs, no solver arithmetic).
 Every function follows a passage of the paper (Ma, Deshmukh, Yokota,
 "Scalable Linear Time Dense Direct Solver for 3-D Problems Without Trailing
 Sub-Matrix Dependencies", arXiv 2208.10907).  Where the paper is silent the
-reading taken is named (O-1 ... O-12) and listed in the design doc.
+reading taken is named (O-1 ... O-12) at the code that applies it.
 
 Notation (Sec. II-A, Fig. "notation"): a box I at level l owns n_I
 "level coordinates"; Q_I = [U^R_I U^S_I] is its orthogonal basis, r_I its
