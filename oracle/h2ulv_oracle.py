@@ -426,16 +426,35 @@ class ULVFactor:
       5. merge of the children's S^SS blocks into the parent level
          (Sec. II-C, the merge equation), then the dense LU of the level
          l_top matrix (eq. BLR2final).
-    ``literal_fill`` forms the fill-in block row explicitly (small cases);
-    otherwise its Gram matrix sum_K A_IK M_K A_IK^T, M_K = A_KK^-1 (sum_J
-    A_KJ A_KJ^T) A_KK^-T, which has the same pivoted QR (pinned by tests).
+
+    ``route`` selects how step 2 forms the block row (all three give the
+    same pivoted QR in exact arithmetic; pinned against each other):
+      "literal": every T_{I,K,J} is formed and the pivoted QR runs on the
+                 explicit block row (the paper's statement; small cases),
+                 after the row fold that keeps its pivots and R (fold_rows);
+      "qr"     : (default) the fill-ins that share K share the row factor
+                 A_KK^-1 [A_KJ]_J, whose QR R-factor R_K is taken once, so
+                 row I holds the n x n blocks A_IK A_KK^-1 R_K^T instead of
+                 one block per J (same column space: [A_KJ]_J = R_K^T Q^T
+                 with Q orthonormal); the block row is folded by Householder
+                 QR and pivoted QR decides, all in FP64 without squaring;
+      "gram"   : the Gram matrix sum_K A_IK M_K A_IK^T + G G^T, M_K =
+                 A_KK^-1 (sum_J A_KJ A_KJ^T) A_KK^-T, and pivoted Cholesky
+                 (the mixed-precision GPU route; it resolves the block row
+                 only to about sqrt(eps) of its norm).
+    ``tol_basis`` overrides the rank tolerance of step 2 (the problem's tol
+    by default).
     """
 
-    def __init__(self, pb, literal_fill=False, spd=False):
+    def __init__(self, pb, route="qr", spd=False, tol_basis=None):
+        if route not in ("qr", "literal", "gram"):
+            raise ValueError(route)
         self.pb = pb
         self.spd = spd
+        self.route = route
         L, boxes, near, far = pb.L, pb.boxes, pb.near, pb.far
-        tol, max_rank = pb.tol, pb.max_rank
+        tol = pb.tol if tol_basis is None else tol_basis
+        max_rank = pb.max_rank
         cand = [np.arange(s, e) for (s, e) in boxes[L]]
         T = [None] * len(cand)           # level coords = T @ point form (None = identity)
         A = {}
@@ -448,19 +467,28 @@ class ULVFactor:
             nb = len(boxes[l])
             n = [len(c) for c in cand]
             # --- 1. fill-ins (Sec. III-B) --------------------------------
-            Minv = {}
             lus = {}
+            Z = {}       # "qr": A_KK^-1 R_K^T
+            Minv = {}    # "gram": A_KK^-1 (sum_J A_KJ A_KJ^T) A_KK^-T
+            Wlit = {}    # "literal": A_KK^-1 A_KJ
             for K in range(nb):
                 others = [J for J in near[l][K] if J != K]
                 if not others:
                     continue
                 lus[K] = sla.lu_factor(A[(K, K)])
-                if not literal_fill:
+                if route == "literal":
+                    # the triangular solves are shared by every row I (Sec. III-B)
+                    for J in others:
+                        Wlit[(K, J)] = sla.lu_solve(lus[K], A[(K, J)])
+                elif route == "qr":
+                    RK = fold_rows(np.hstack([A[(K, J)] for J in others]).T)
+                    Z[K] = sla.lu_solve(lus[K], RK.T)
+                elif route == "gram":
                     NG = np.zeros((n[K], n[K]))
                     for J in others:
                         NG += A[(K, J)] @ A[(K, J)].T
-                    Z = sla.lu_solve(lus[K], NG)
-                    Minv[K] = sla.lu_solve(lus[K], Z.T).T
+                    Zg = sla.lu_solve(lus[K], NG)
+                    Minv[K] = sla.lu_solve(lus[K], Zg.T).T
             # --- 2. bases (eq. fillu) -------------------------------------
             Q, W, sk, r = [], [], [], []
             for I in range(nb):
@@ -468,9 +496,12 @@ class ULVFactor:
                 G = kernel_matrix(pb.kernel, pb.Xt[cand[I]], pb.Xt[fs], same=True, **pb.kp) \
                     if len(fs) else np.zeros((n[I], 0))
                 Kn = [K for K in near[l][I] if K != I and K in lus]
-                if literal_fill:
-                    Fblocks = [A[(I, K)] @ sla.lu_solve(lus[K], A[(K, J)])
-                               for K, J in fill_in_terms(near[l], I) if K in lus]
+                if route in ("literal", "qr"):
+                    if route == "literal":
+                        Fblocks = [A[(I, K)] @ Wlit[(K, J)]
+                                   for K, J in fill_in_terms(near[l], I) if K in lus]
+                    else:
+                        Fblocks = [A[(I, K)] @ Z[K] for K in Kn]
                     F = np.hstack(Fblocks) if Fblocks else np.zeros((n[I], 0))
                     if T[I] is not None:
                         F = sla.solve(T[I], F)
@@ -478,7 +509,7 @@ class ULVFactor:
                     if B.shape[1] == 0 or not np.any(B):
                         piv, R, rk = np.arange(n[I]), None, 0
                     else:
-                        piv, R, rk = pivoted_qr(B.T, tol, max_rank)
+                        piv, R, rk = pivoted_qr(fold_rows(B.T), tol, max_rank)
                 else:
                     Gr = G @ G.T
                     if Kn:

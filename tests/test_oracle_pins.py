@@ -88,6 +88,42 @@ def test_far_samples_rule():
     assert len(exact) + sum(e - s for j in pb.near[l][i] for (s, e) in [pb.boxes[l][j]]) == 4096
 
 
+def _golden(name):
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", name)))
+
+
+def test_far_samples_positions_hand_computed():
+    """Positions of the deterministic far-field sample of one leaf, its far
+    lists at every level and l_top, against values worked out by hand
+    (fixture tests/golden/far_samples_line64.json, with its derivation)."""
+    fx = _golden("far_samples_line64.json")
+    X = np.stack([np.arange(64.0), np.zeros(64), np.zeros(64)], 1)
+    pb = O.Problem(X, "laplace", 4, 1.0, 1e-8, 4, s0=fx["s0"], s_min=fx["s_min"])
+    assert pb.L == 4 and list(pb.perm) == list(range(64))
+    i = fx["box"]
+    for lev, lst in fx["far"].items():
+        a = i >> (pb.L - int(lev))
+        assert pb.far[int(lev)][a] == lst, (lev, pb.far[int(lev)][a])
+    got = O.far_samples(pb.boxes, pb.far, fx["level"], i, fx["s0"], fx["s_min"])
+    assert got.tolist() == fx["samples"]
+    assert pb.ltop == fx["l_top"]
+
+
+def test_admissibility_closed_forms():
+    """O-2 on unit boxes: max(diam) = sqrt(3); a face gap of 2 is far for
+    eta = 1 and near for eta = 0.8 (0.8 * 2 < sqrt(3)); a corner gap of
+    sqrt(3) sits exactly on the boundary (far for eta = 1, near just below)."""
+    u = (np.zeros(3), np.ones(3))
+    face = (np.array([3.0, 0, 0]), np.array([4.0, 1, 1]))
+    corner = (np.full(3, 2.0), np.full(3, 3.0))
+    overlap = (np.full(3, 0.5), np.full(3, 1.5))
+    assert O.admissible(u, face, 1.0) and not O.admissible(u, face, 0.8)
+    assert O.admissible(u, corner, 1.0) and not O.admissible(u, corner, 0.999)
+    assert not O.admissible(u, overlap, 1e12)
+
+
 # ------------------------------------------------------ pivoted QR and ID --
 def _lowrank(m, n, r, seed):
     rng = np.random.default_rng(seed)
@@ -161,26 +197,53 @@ def test_all_near_degenerates_to_dense_lu():
 def test_hss_special_case_matches_dense():
     """Points on a line with eta -> infinity: every off-diagonal pair is far
     at level 1 (weak admissibility), there are no fill-ins and the method is
-    the paper's HSS-ULV.  Its solve must agree with dense LU to ~tol."""
+    the paper's HSS-ULV (Sec. II-C).  Its solve and log-det must agree with
+    dense LU to about tol."""
     X = line_points(1024, 5)
     tol = 1e-10
     pb = O.Problem(X, "laplace", 64, 1e12, tol, 1 << 30, s0=0)
     assert all(pb.near[pb.L][i] == [i] for i in range(2 ** pb.L))
+    assert pb.ltop == 0 and pb.L == 4
     op = O.H2Operator(pb)
     A = O.kernel_matrix("laplace", X, X)
     b = np.random.default_rng(6).standard_normal(1024)
     xd = np.linalg.solve(A, b)
-    # Householder route (block row formed explicitly): exact to ~tol.
-    F1 = O.ULVFactor(pb, literal_fill=True)
-    x0 = F1.solve(b)
-    assert np.linalg.norm(x0 - xd) / np.linalg.norm(xd) < 1e3 * tol
-    assert F1.logdet()[0] == pytest.approx(np.linalg.slogdet(A)[1], rel=1e-10)
+    ld_dense = np.linalg.slogdet(A)[1]
+    # the paper's route (Householder QR of the block row, default) and the
+    # literal one: exact to about tol, unrefined
+    for route in ("qr", "literal"):
+        F1 = O.ULVFactor(pb, route=route)
+        assert all(0 < r < 64 for r in F1.rank_log[0][1])
+        x0 = F1.solve(b)
+        assert np.linalg.norm(x0 - xd) / np.linalg.norm(xd) < 1e3 * tol
+        assert F1.logdet()[0] == pytest.approx(ld_dense, rel=1e-12)
     # Gram route (limited to ~sqrt(eps) in the basis): refinement restores it.
-    F = O.ULVFactor(pb)
+    F = O.ULVFactor(pb, route="gram")
     x, rel, it = O.refine(op, F, b, 1e-12, 10)
     assert rel[0] <= 1e-12
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e3 * tol
-    assert F.logdet()[0] == pytest.approx(np.linalg.slogdet(A)[1], rel=1e-8)
+    assert F.logdet()[0] == pytest.approx(ld_dense, rel=1e-8)
+
+
+def test_blr2_special_case_one_level():
+    """One level (L = 1) with the two halves far from each other: the
+    paper's BLR^2-ULV (Sec. II-B, eq. lu ... eq. BLR2final) with shared
+    bases, one partial LU per box and the dense LU of the merged skeleton
+    matrix.  No fill-ins; exact to about tol against dense LU."""
+    X = line_points(512, 13)
+    tol = 1e-10
+    pb = O.Problem(X, "yukawa", 256, 1e12, tol, 256, s0=0)
+    assert pb.L == 1 and pb.ltop == 0 and pb.far[1] == [[1], [0]]
+    F = O.ULVFactor(pb)
+    (l, r), = F.rank_log
+    assert l == 1 and all(0 < q < 256 for q in r)
+    assert F.root_dense.shape == (sum(r), sum(r))
+    A = O.kernel_matrix("yukawa", X, X)
+    b = np.random.default_rng(14).standard_normal(512)
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(F.solve(b) - xd) / np.linalg.norm(xd) < 1e3 * tol
+    sg, ld = np.linalg.slogdet(A)
+    assert F.logdet()[0] == pytest.approx(ld, rel=1e-12) and F.logdet()[1] == sg
 
 
 def test_orthonormal_bases():
@@ -208,16 +271,28 @@ def test_h2_operator_accuracy(s0):
 
 
 # ---------------------------------------------------------- fill-in forms --
-def test_literal_fill_in_block_row_equals_gram_route():
-    X = synth.sphere_ball(1024, 12)
-    pb = O.Problem(X, "laplace", 64, 1.0, 1e-6, 40)
-    F1 = O.ULVFactor(pb, literal_fill=True)
-    F2 = O.ULVFactor(pb, literal_fill=False)
-    for (l1, r1), (l2, r2) in zip(F1.rank_log, F2.rank_log):
-        assert r1 == r2
-    b = np.random.default_rng(1).standard_normal(1024)
-    x1, x2 = F1.solve(b), F2.solve(b)
-    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-6
+def test_fill_in_routes_agree_on_a_multilevel_case():
+    """The three forms of the fill-in block row (eq. fillu) on a surface
+    cloud with two ULV levels and fill-ins at both (N = 2048, leaf 64,
+    tol 1e-6): the default route (per-K QR compression of the fill-in rows)
+    and the literal one (every T_{I,K,J} formed) choose the same ranks and
+    give the same factorization to rounding; the Gram route agrees at this
+    tolerance (above its sqrt(eps) resolution)."""
+    X = synth.surface_union(2048, 4)
+    pb = O.Problem(X, "laplace", 64, 1.0, 1e-6, 64)
+    assert pb.L - pb.ltop == 2
+    F1 = O.ULVFactor(pb, route="literal")
+    F2 = O.ULVFactor(pb, route="qr")
+    F3 = O.ULVFactor(pb, route="gram")
+    assert any(r < 64 for r in F1.rank_log[0][1])        # something is eliminated
+    for (l1, r1), (l2, r2), (l3, r3) in zip(F1.rank_log, F2.rank_log, F3.rank_log):
+        assert r1 == r2 == r3
+    assert F2.logdet()[0] == pytest.approx(F1.logdet()[0], rel=1e-13)
+    assert F3.logdet()[0] == pytest.approx(F1.logdet()[0], rel=1e-10)
+    b = np.random.default_rng(1).standard_normal(2048)
+    x1, x2, x3 = F1.solve(b), F2.solve(b), F3.solve(b)
+    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-11
+    assert np.linalg.norm(x1 - x3) / np.linalg.norm(x1) < 1e-6
 
 
 # ------------------------------------------------ brute force, small N ----
