@@ -104,9 +104,87 @@ def cpu_oracle_sample(n_sample, repeats=1):
         pass
     fac_solve = float(np.median([t[1] for t in ts]))
     return dict(value=fac_solve * W["n"] / n_sample, unit="s", cores=int(cores), kind="oracle",
+                cpu_model=cpu_model(), measured_s=fac_solve, n_sample=n_sample,
                 sample=f"oracle factor+refined solve on N={n_sample} points of the same surface union "
                        f"(leaf 256, tol 1e-6), {fac_solve:.2f} s measured, scaled x{W['n'] / n_sample:.0f} "
                        f"to N=2^20 (O(N) method); construct {np.median([t[0] for t in ts]):.2f} s not included")
+
+
+# DRAM traffic per launch of the dominant kernel, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel@site; None
+# until a capture of the current kernel exists.
+NCU_TRAFFIC = {}
+
+FP32_PREFIX = ("gemm_f32", "kgram_f32", "getrf_f32", "trsm_f32", "hqr_f32")
+FP64_PREFIX = ("gemm_f64", "getrf_f64", "trsm_f64", "pchol_f64", "pqr_f64", "fold_f64", "hqr_f64", "kgram_f64")
+
+
+def roofline_of(name, ks, pk, tot_ms):
+    """Achieved = algorithmic flops or bytes the host declared for the
+    kernel's launches / their summed CUDA-event time; peak by the bound."""
+    secs = ks["ms"] * 1e-3
+    clock = (pk["sm_max_mhz"] if pk else 2070.0) * 1e6
+    if name.startswith("gemm_tc3xtf32"):
+        # split 3xTF32: three tf32 products per useful product; tf32 peak =
+        # measured sustained bf16 x nominal tf32/bf16 (1.1 / 2.25)
+        peak = (pk["bf16_tflops_sustained"] if pk else 1700.0) * (1.1 / 2.25) / 3.0
+        bound, unit, ach = "tensor", "TFLOP/s", ks["flops"] / secs / 1e12
+        src = "measured sustained bf16 x tf32/bf16 nominal / 3 products" + ("" if pk else " (fallback)")
+    elif name.startswith(FP32_PREFIX) and ks["flops"] > 0:
+        peak = 152 * 128 * 2 * clock / 1e12
+        bound, unit, ach = "alu", "TFLOP/s", ks["flops"] / secs / 1e12
+        src = "152 SM x 128 FP32 lanes x 2 x max SM clock"
+    elif name.startswith(FP64_PREFIX) and ks["flops"] > 0:
+        peak = 1.25 * clock / 2.07e9
+        bound, unit, ach = "alu", "TFLOP/s", ks["flops"] / secs / 1e12
+        src = "GB300 nominal FP64 1.25 TFLOP/s at the max SM clock"
+    else:
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        bound, unit, ach = "hbm", "GB/s", ks["bytes"] / secs / 1e9
+        src = "measured HBM copy bandwidth" if pk else "fallback 6.8 TB/s"
+    tr = NCU_TRAFFIC.get(name)
+    return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+            "frac": ach / peak if peak else None, "traffic": tr["bytes_per_launch"] if tr else None,
+            "traffic_source": tr["source"] if tr else None, "launches": ks["launches"],
+            "ms_total": ks["ms"], "share": ks["ms"] / tot_ms, "per_launch_ms": ks["ms"] / max(1, ks["launches"]),
+            "algorithmic_per_launch": (ks["flops"] if bound != "hbm" else ks["bytes"]) / max(1, ks["launches"]),
+            "peak_source": src}
+
+
+def dense_rows(X, rows, v, delta=1e-3):
+    """(K v)_i on sampled rows of the workload's dense matrix, K = 1/(r +
+    delta) (Laplace), one FP64 row at a time."""
+    return np.array([(1.0 / (np.sqrt(((X - X[i]) ** 2).sum(1)) + delta)) @ v for i in rows])
+
+
+def accuracy(h, H, b_dev, b_host, X, rows, x_ref):
+    """The factorization's own accuracy: x_u = ULV^-1 b (no refinement); its
+    dense residual on sampled rows, its distance to the refined solution
+    x_ref (which solves the H2 system to 1e-10), and the dense residual of
+    x_ref itself."""
+    import torch
+    n = len(b_host)
+    xu = torch.zeros_like(b_dev)
+    st, ach, it = H.h2_solve(h, b_dev, xu, 1, n, 1e300, 0)
+    xu = xu.cpu().numpy()
+    assert WORKLOAD["kernel"] == "laplace"
+    r_u = b_host[rows] - dense_rows(X, rows, xu)
+    r_x = b_host[rows] - dense_rows(X, rows, x_ref)
+    nb = np.linalg.norm(b_host[rows])
+    return {"unrefined_h2_residual": float(ach[0]),
+            "unrefined_dense_residual_rows": float(np.linalg.norm(r_u) / nb),
+            "unrefined_vs_refined": float(np.linalg.norm(xu - x_ref) / np.linalg.norm(x_ref)),
+            "refined_dense_residual_rows": float(np.linalg.norm(r_x) / nb)}
+
+
+def cpu_model():
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True).stdout.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
 
 
 def dist_init(world):
@@ -210,9 +288,10 @@ def main():
     # ---- warm-up
     for _ in range(args.warmup):
         step(H.H2_MIXED, b, x)
-    # ---- timed region (device-resident inputs), per-kernel events on
+    # ---- timed region: device-resident inputs, no instrumentation (the
+    # solve plans run as captured CUDA graphs)
+    H.h2_profile(0, 1)
     clocks = ClockSampler(local)
-    H.h2_profile(1, 1)
     barrier()
     clocks.start()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -227,59 +306,47 @@ def main():
         iters.append((int(st), float(ach[0]), int(it)))
     barrier()
     clk = clocks.stop()
+    launches_timed = int(json.loads(H.h2_stats(h)).get("launches", 0))
     total_ms = evs[0].elapsed_time(evs[-1])
-    stats = json.loads(H.h2_stats(h))
-    H.h2_profile(0, 0)
-    if args.kernel_table:
-        ks_ = sorted(stats.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])
-        tot_ = sum(v["ms"] for _, v in ks_) or 1.0
-        print(f"per-kernel CUDA-event times over {args.steps} timed step(s)", file=sys.stderr)
-        for k_, v_ in ks_[:40]:
-            print(f"{k_:32s} launches {v_['launches']:6d} ms {v_['ms']:10.2f} ({100 * v_['ms'] / tot_:5.1f}%) "
-                  f"GFLOP {v_['flops'] / 1e9:10.1f}", file=sys.stderr)
     f_ms = [evs[k].elapsed_time(evf[k]) for k in range(args.steps)]
     s_ms = [evf[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     step_ms = total_ms / args.steps
     solve_ms = float(np.mean(s_ms))
     step_ms = max_over_ranks(step_ms, world, dev)
 
-    # ---- roofline of the dominant kernel (event times inside the timed region)
+    # ---- per-kernel times: the same step repeated with every launch
+    # bracketed by CUDA events on its stream (rooflines below)
+    prof_steps = min(args.steps, 3)
+    H.h2_profile(1, 1)
+    barrier()
+    for _ in range(prof_steps):
+        step(H.H2_MIXED, b, x)
+    barrier()
+    stats = json.loads(H.h2_stats(h))
+    H.h2_profile(0, 0)
     kern_stats = stats.get("kernels", {})
+    if args.kernel_table:
+        ks_ = sorted(kern_stats.items(), key=lambda kv: -kv[1]["ms"])
+        tot_ = sum(v["ms"] for _, v in ks_) or 1.0
+        print(f"per-kernel CUDA-event times over {prof_steps} instrumented step(s)", file=sys.stderr)
+        for k_, v_ in ks_[:48]:
+            print(f"{k_:32s} launches {v_['launches']:6d} ms {v_['ms']:10.2f} ({100 * v_['ms'] / tot_:5.1f}%) "
+                  f"GFLOP {v_['flops'] / 1e9:10.1f} GB {v_['bytes'] / 1e9:9.2f}", file=sys.stderr)
+
+    # ---- roofline of every kernel (algorithmic flops or bytes per launch
+    # over its event time); the dominant one goes in "roofline"
     pk = peaks()
-
-    def roofline_of(name, ks):
-        per_launch_ms = ks["ms"] / max(1, ks["launches"])
-        secs = ks["ms"] * 1e-3
-        if name.startswith(("symv_pairs", "gemv", "gather", "copy")):
-            # HBM: algorithmic bytes (every stored operand read once) per second
-            peak = pk["hbm_gbs"] if pk else 6800.0
-            bound, unit, ach = "hbm", "GB/s", (ks["bytes"] / secs / 1e9 if secs > 0 else 0.0)
-            src = "measured HBM copy bandwidth (MEASURED_PEAKS.json)" if pk else "fallback 6.8 TB/s"
-        elif name.startswith(("gemm_tc", "tc_")):
-            # split 3xTF32: three tf32 products per useful product; tf32 peak =
-            # measured sustained bf16 x nominal tf32/bf16 (1.1 / 2.25)
-            peak = (pk["bf16_tflops_sustained"] if pk else 1700.0) * (1.1 / 2.25) / 3.0
-            bound, unit, ach = "tensor", "TFLOP/s", ks["flops"] / secs / 1e12 if secs > 0 else 0.0
-            src = "measured sustained bf16 (MEASURED_PEAKS.json) x tf32/bf16 nominal / 3 products"
-        elif name.startswith(("gemm_f32", "kgram_f32")):
-            # FP32 SIMT FMA pipe: 152 SMs x 128 lanes x 2 flop x max SM clock
-            peak = 152 * 128 * 2 * (pk["sm_max_mhz"] if pk else 2070.0) * 1e6 / 1e12
-            bound, unit, ach = "alu", "TFLOP/s", ks["flops"] / secs / 1e12 if secs > 0 else 0.0
-            src = "152 SM x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS.json)"
-        else:
-            # FP64 DFMA pipe: GB300 nominal 1.25 TFLOP/s dense FP64
-            peak = 1.25 * (pk["sm_max_mhz"] / 2070.0 if pk else 1.0)
-            bound, unit, ach = "alu", "TFLOP/s", ks["flops"] / secs / 1e12 if secs > 0 else 0.0
-            src = "GB300 nominal FP64 1.25 TFLOP/s at the measured max SM clock"
-        return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                "frac": ach / peak if peak else None, "traffic": None, "launches": ks["launches"],
-                "ms_total": ks["ms"], "share": ks["ms"] / max(1e-9, sum(v["ms"] for v in kern_stats.values())),
-                "per_launch_ms": per_launch_ms, "peak_source": src,
-                "traffic_note": "ncu DRAM bytes of one captured launch of a smaller case are in profiles/"}
-
+    tot_ms = sum(v["ms"] for v in kern_stats.values()) or 1.0
     ranked = sorted(kern_stats.items(), key=lambda kv: -kv[1]["ms"])
-    roof = roofline_of(*ranked[0]) if ranked else None
-    roof_top = [roofline_of(k, v) for k, v in ranked[:4]]
+    roof_all = [roofline_of(k, v, pk, tot_ms) for k, v in ranked if v["ms"] > 0]
+    roof = roof_all[0] if roof_all else None
+
+    # ---- accuracy of the factorization itself (the paper's protocol: the
+    # unrefined ULV solution), on sampled rows of the dense kernel matrix
+    rows = np.sort(np.random.default_rng(77).choice(n, 48, replace=False))
+    x_ref = x.cpu().numpy()
+    acc = {"rows": len(rows), "mixed": accuracy(h, H, b, b_host, X, rows, x_ref)}
 
     # ---- FP64 path, same GPU (fewer steps: FP64 throughput is 1/60 of FP32)
     fp64 = None
@@ -300,21 +367,21 @@ def main():
             fs.append(e0.elapsed_time(e1))
             ss.append(e1.elapsed_time(e2))
             its.append(it)
+        st64 = json.loads(H.h2_stats(h))
         fp64 = {"factor_s": float(np.median(fs)) / 1e3, "solve_ms": float(np.median(ss)), "iters": its,
-                "step_s": (float(np.median(fs)) + float(np.median(ss))) / 1e3}
+                "step_s": (float(np.median(fs)) + float(np.median(ss))) / 1e3,
+                "basis_route": st64.get("basis_route"), "tol_basis": st64.get("tol_basis")}
+        acc["fp64"] = accuracy(h, H, b, b_host, X, rows, x.cpu().numpy())
+        H.h2_factor(h, H.H2_MIXED)
 
     # ---- end to end through the C ABI with host buffers (pinned)
     b_pin = torch.from_numpy(b_host).pin_memory()
     x_pin = torch.zeros_like(b_pin).pin_memory()
     step(H.H2_MIXED, b_pin, x_pin)
     barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
     t_e2e = time.perf_counter()
     for _ in range(args.steps):
         step(H.H2_MIXED, b_pin, x_pin)
-    e1.record(stream)
     barrier()
     e2e_ms = (time.perf_counter() - t_e2e) * 1e3 / args.steps
 
@@ -324,6 +391,7 @@ def main():
         cpu = cpu_oracle_sample(args.cpu_sample)
 
     if rank == 0:
+        st_m = json.loads(H.h2_stats(h))
         line = {
             "metric": METRIC, "value": step_ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
@@ -333,17 +401,24 @@ def main():
                                    "leaf 256, eta 1, tol 1e-6, mixed factor refined to H2 residual 1e-10",
                        "n": n, "leaf": W["leaf"], "eta": W["eta"], "tol": W["tol"], "max_rank": W["max_rank"],
                        "far_sample": [W["far_s0"], W["far_smin"]], "l2": "inputs larger than L2 (tens of GB)",
+                       "residual": "FP64 H2 operator; its near field for one right-hand side in double-float "
+                                   "(FP64 entries split exactly into FP32 pairs, about 2^-46 per product)",
+                       "basis": {"route": st_m.get("basis_route"), "tol_basis": st_m.get("tol_basis")},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "factor_s": float(np.mean(f_ms)) / 1e3, "solve_ms": solve_ms,
+            "step_s_median": float(np.median(per_step)) / 1e3,
+            "step_s_all": [round(v / 1e3, 4) for v in per_step],
             "refine": [{"status": s_, "residual": a_, "iters": i_} for s_, a_, i_ in iters],
             "construct_s": t_construct,
             "fp64": fp64,
             "mixed_vs_fp64_speedup": (fp64["step_s"] / (step_ms / 1e3)) if fp64 else None,
+            "accuracy": acc,
             "roofline": roof,
-            "roofline_top": roof_top,
+            "roofline_all": roof_all,
+            "roofline_steps": prof_steps,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
-            "gpu_launches": int(stats.get("launches", 0)),
+            "gpu_launches": launches_timed,
             "clocks": clk,
             "levels": stats.get("levels"),
         }

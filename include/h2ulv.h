@@ -123,7 +123,21 @@ h2_status h2_construct_batched(int32_t P, const double* const* points, const int
  *   precision : H2_FP64 or H2_MIXED
  *   spd       : nonzero = Cholesky instead of LU (symmetric positive
  *               definite kernels only)
- * Errors: H2_ERR_SINGULAR, H2_ERR_NOT_SPD, H2_ERR_OOM, H2_ERR_DEVICE. */
+ * Basis of each box (eq. fillu), by one of two routes:
+ *   "qr"   : Householder QR of the block row [fill-ins | far field] (the
+ *            fill-ins sharing a box K enter as A_IK A_KK^-1 R_K^T, R_K the
+ *            QR triangle of [A_KJ]_J^T), then column-pivoted QR; resolves
+ *            the block row to FP64 rounding.  H2_FP64 with tol < 2^-20.
+ *   "gram" : the Gram matrix of the same block row and pivoted Cholesky
+ *            (same pivots in exact arithmetic); it resolves the block row
+ *            only to about sqrt(eps) of its norm in FP64 and 2^-10 in FP32.
+ *            H2_FP64 with tol >= 2^-20 (tol used as given) and H2_MIXED
+ *            (FP32 on the tensor cores, rank tolerance max(tol, 2^-10);
+ *            the factors precondition the FP64 refinement).
+ * h2_stats reports the route ("basis_route": "qr" or "gram") and the
+ * tolerance the bases used ("tol_basis").
+ * Errors: H2_ERR_SINGULAR, H2_ERR_NOT_SPD, H2_ERR_NONFINITE (non-finite
+ * value in a block row), H2_ERR_OOM, H2_ERR_DEVICE, H2_ERR_TIMEOUT. */
 h2_status h2_factor(h2_handle h, int32_t precision, int32_t spd);
 
 /* Solve A x = b with the ULV factors (Sec. II-B: L z = U^T b, U y = z,
@@ -167,6 +181,9 @@ h2_status h2_logdet(h2_handle h, double* log_abs_det, int32_t* sign);
  *     the library until the process exits; nothing is allocated per call.
  *   - Limit: at most 16384 factored blocks per tree height; larger handles
  *     are rejected with H2_ERR_ARG.
+ *   - The array used is the one on the device that was current when the
+ *     handle was constructed (the call makes that device current and
+ *     restores the caller's current device before returning).
  *   - The first call on a device looks up the array's device address (once
  *     per device); make that first call before any stream capture.
  *   - Every call shares the array and it keeps the last call's contents;
@@ -174,8 +191,9 @@ h2_status h2_logdet(h2_handle h, double* log_abs_det, int32_t* sign);
  *     once) race on it and must be serialised by the caller. */
 h2_status h2_logdet_noalloc(h2_handle h, double* log_abs_det, int32_t* sign);
 
-/* JSON statistics: per-level ranks, flops, bytes, times (ms); cap = size of
- * the host buffer json.  Truncated output is still NUL-terminated. */
+/* JSON statistics: per-level ranks, flops, bytes, times (ms), the basis
+ * route and effective rank tolerance of the last factorization; cap = size
+ * of the host buffer json.  Truncated output is still NUL-terminated. */
 h2_status h2_stats(h2_handle h, char* json, size_t cap);
 
 /* Per-kernel instrumentation shared by all handles of the process.  Every

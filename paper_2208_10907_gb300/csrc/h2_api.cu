@@ -394,45 +394,139 @@ static size_t chunk_pairs(std::vector<PairSlot>& v, size_t p0, size_t budget) {
   return p1;
 }
 
+// Algorithmic work of the batched dense kernels (flops and the bytes their
+// operands and results occupy, each counted once), noted for the profiler
+// before each launch.  LU of an m x c panel: m c^2 - c^3/3 flops; triangular
+// solve of n x n with r right-hand sides: n^2 r; Householder QR of n x r with
+// the full n x n Q formed: 2 r^2 (n - r/3) + 4 n^2 r - 2 n r^2; far-field
+// Gram of n candidates and m samples: 2 n^2 m (plus 2 n m kernel values).
+static double work_getrf(const std::vector<LuTask>& v, size_t es, double& bytes) {
+  double f = 0.0;
+  bytes = 0.0;
+  for (const LuTask& t : v) {
+    f += (double)t.m * t.nc * t.nc - (double)t.nc * t.nc * t.nc / 3.0;
+    bytes += 2.0 * es * t.m * t.nc;
+  }
+  return f;
+}
+static double work_trsm(const std::vector<TrsmTask>& v, size_t es, double& bytes) {
+  double f = 0.0;
+  bytes = 0.0;
+  for (const TrsmTask& t : v) {
+    f += (double)t.n * t.n * t.nrhs;
+    bytes += es * (0.5 * t.n * t.n + 2.0 * t.n * t.nrhs);
+  }
+  return f;
+}
+static double work_copy(const std::vector<CopyTask>& v, size_t es_s, size_t es_d) {
+  double b = 0.0;
+  for (const CopyTask& t : v) b += (double)(es_s + es_d) * t.rows * t.cols;
+  return b;
+}
+
 // Validate (H2_CHECK=1), upload and launch.
 static void run_trsm(Prec p, bool lower, bool unit, bool tr, const std::vector<TrsmTask>& v, int maxrhs, Scratch& sc) {
   if (v.empty()) return;
   validate(v, esz(p));
+  double by = 0.0, f = work_trsm(v, esz(p), by);
+  prof_note(f, by);
   launch_trsm(p, lower, unit, tr, sc.up(v), (int)v.size(), maxrhs, sc.s);
 }
 static void run_getrf(Prec p, const std::vector<LuTask>& v, Scratch& sc) {
   if (v.empty()) return;
   validate(v, esz(p));
+  double by = 0.0, f = work_getrf(v, esz(p), by);
+  prof_note(f, by);
   launch_getrf(p, sc.up(v), (int)v.size(), sc.s);
 }
 static void run_copy(Prec a, Prec b, bool tr, const std::vector<CopyTask>& v, int mr, int mc, Scratch& sc) {
   if (v.empty()) return;
   validate(v, esz(a), esz(b), tr);
+  prof_note(0.0, work_copy(v, esz(a), esz(b)));
   launch_copy(a, b, tr, sc.up(v), (int)v.size(), mr, mc, sc.s);
 }
+// The pivoted Cholesky's work depends on the ranks it finds; it is added
+// once they are read back (prof_add), at n r^2 - 2 r^3 / 3 flops per box.
 static void run_pchol(const std::vector<CholTask>& v, Scratch& sc) {
   if (v.empty()) return;
   validate(v);
+  double by = 0.0;
+  for (const CholTask& t : v) by += 16.0 * t.n * t.n;
+  prof_note(0.0, by);
   launch_pchol(sc.up(v), (int)v.size(), sc.s);
 }
 static void run_kgram(Prec p, const std::vector<KgramTask>& v, int maxn, Points pts, KParams kp, Scratch& sc) {
   if (v.empty()) return;
   validate(v);
+  double f = 0.0, by = 0.0;
+  for (const KgramTask& t : v) {
+    f += 2.0 * t.n * t.n * t.m;
+    by += 8.0 * t.n * t.n * (t.accumulate ? 2.0 : 1.0);
+  }
+  prof_note(f, by);
   launch_kgram(p, sc.up(v), (int)v.size(), maxn, pts, kp, sc.s);
 }
 static void run_assemble(Prec p, const std::vector<AsmTask>& v, int mr, int mc, Points pts, KParams kp, Scratch& sc) {
   if (v.empty()) return;
   validate(v, esz(p));
+  double by = 0.0;
+  for (const AsmTask& t : v) by += (double)esz(p) * t.nr * t.nc;
+  prof_note(0.0, by);
   launch_assemble(p, sc.up(v), (int)v.size(), mr, mc, pts, kp, sc.s);
 }
 static void run_hqr(Prec p, const std::vector<HqrTask>& v, Scratch& sc) {
   if (v.empty()) return;
   validate(v, esz(p));
+  double f = 0.0, by = 0.0;
+  for (const HqrTask& t : v) {
+    const double n = t.n, r = t.r;
+    f += 2.0 * r * r * (n - r / 3.0) + 4.0 * n * n * r - 2.0 * n * r * r;
+    by += (double)esz(p) * (2.0 * n * r + n * n + r * r);
+  }
+  prof_note(f, by);
   launch_hqr(p, sc.up(v), (int)v.size(), sc.s);
+}
+// Folds declare 2 rows n^2 flops per folded row block (a Householder QR of
+// the rows appended to an n x n triangle) and the explicit rows' bytes.
+static void run_fold(const std::vector<FoldTask>& v, const std::vector<FoldTerm>& terms, Points pts, KParams kp,
+                     Scratch& sc) {
+  if (v.empty()) return;
+  double flops = 0.0, bytes = 0.0;
+  for (const FoldTask& t : v) {
+    double rows = t.m;
+    for (int q = t.t0; q < t.t0 + t.nt; ++q) {
+      rows += terms[q].rows;
+      bytes += 8.0 * terms[q].rows * t.n;
+    }
+    flops += 2.0 * rows * t.n * t.n;
+    bytes += 16.0 * t.n * t.n;
+  }
+  if (g_check)
+    for (const FoldTask& t : v) {
+      check_range(t.R, (size_t)t.n * t.n * 8, "fold R");
+      for (int q = t.t0; q < t.t0 + t.nt; ++q) {
+        const FoldTerm& f = terms[q];
+        check_range(f.X, (f.tr ? ext(f.rows, t.n, f.ld) : ext(t.n, f.rows, f.ld)) * 8, "fold rows");
+      }
+    }
+  prof_note(flops, bytes);
+  launch_fold(sc.up(v), (int)v.size(), sc.up(terms), pts, kp, sc.s);
+}
+// Column-pivoted QR of an n x n triangle stopped at rank r: 4 n^2 r -
+// 2 (n + n) r^2 + 4 r^3 / 3 flops, added once the ranks are read back.
+static void run_pqr(const std::vector<PqrTask>& v, Scratch& sc) {
+  if (v.empty()) return;
+  double by = 0.0;
+  for (const PqrTask& t : v) by += 16.0 * t.n * t.n;
+  prof_note(0.0, by);
+  launch_pqr(sc.up(v), (int)v.size(), sc.s);
 }
 static void run_interp(Prec p, const std::vector<InterpTask>& v, Scratch& sc) {
   if (v.empty()) return;
   validate(v, esz(p));
+  double by = 0.0;
+  for (const InterpTask& t : v) by += (double)esz(p) * ((double)t.n * t.r + (double)t.r * (t.n - t.r));
+  prof_note(0.0, by);
   launch_interp(p, sc.up(v), (int)v.size(), sc.s);
 }
 
@@ -496,6 +590,7 @@ struct Plan {
     if (v.empty()) return;
     validate(v, esz(p));
     Op o{};
+    o.flops = work_trsm(v, esz(p), o.bytes);
     o.kind = 1;
     o.p = p;
     o.f1 = lower;
@@ -511,6 +606,7 @@ struct Plan {
     if (v.empty()) return;
     validate(v, esz(a), esz(b), tr);
     Op o{};
+    o.bytes = work_copy(v, esz(a), esz(b));
     o.kind = 2;
     o.p = a;
     o.p2 = b;
@@ -688,6 +784,7 @@ struct Problem {
 
 struct Handle {
   cudaStream_t s = nullptr;
+  int dev = 0;                       // device current at construct (owns every buffer of the handle)
   KParams kp{};
   h2_options opt{};
   std::vector<Problem> probs;
@@ -708,6 +805,8 @@ struct Handle {
   std::vector<int64_t> leaf_s;               // global tree-order start per leaf
   bool factored = false;
   int precision = 0, spd = 0;
+  double tol_basis = 0.0;                    // rank tolerance the last factorization's bases used
+  const char* basis_route = "none";          // "qr" or "gram" (route of the last factorization)
   // solve-time plans, per right-hand-side count: workspaces and launch lists
   struct SolvePlans {
     int nrhs = 0;
@@ -951,7 +1050,7 @@ static void build_operator(Handle& h) {
       qt.push_back(PqrTask{R0 + r_off[g], n, n, n, piv + cand_off[g], Rq + r_off[g], rank + g, h.opt.tol,
                            h.opt.max_rank});
     }
-    launch_fold(sc.up(ft), (int)ft.size(), pts, h.kp, s);
+    launch_fold(sc.up(ft), (int)ft.size(), nullptr, pts, h.kp, s);
     launch_pqr(sc.up(qt), (int)qt.size(), s);
     std::vector<int> hr(ht.nb), hpiv(cand_off[ht.nb]);
     H2_CUDA(cudaMemcpyAsync(hr.data(), rank, ht.nb * 4, cudaMemcpyDeviceToHost, s));
@@ -1501,6 +1600,20 @@ static void factor(Handle& h, int precision, int spd) {
       h.worst_bytes += (double)worst * ws;
     }
     // ---------------- 1. fill-ins (Sec. III-B) --------------------------
+    // Two routes to the basis of eq. fillu.
+    // QR route: the fill-ins of row I share, per K, the row factor
+    // A_KK^-1 [A_KJ]_J, whose column space is that of Z_K = A_KK^-1 R_K^T
+    // with R_K the Householder triangle of [A_KJ]_J^T, so row I holds the
+    // n x n blocks V_IK = A_IK Z_K; they and the far field are folded by
+    // Householder QR and the pivoted QR decides (nothing is squared).
+    // Gram route: the Gram matrix of the same block row (sum of GEMMs, on
+    // the tensor cores in mixed precision) and pivoted Cholesky.  Squaring
+    // the block row leaves its Gram with rounding noise of order eps times
+    // its norm, so FP64 keeps the Gram route only while the rank threshold
+    // tol^2 G_11 stays at least 2^12 units of roundoff above that noise
+    // (tol >= 2^6 sqrt(eps) = 2^-20) and takes the QR route below; mixed
+    // precision takes the Gram route with the 2^-10 floor below.
+    const bool qr_route = (W == Prec::F64) && h.opt.tol < 0x1p-20;
     prof_tag("fillin");
     std::vector<int> has_lu(nb, 0);
     for (int g = 0; g < nb; ++g) has_lu[g] = ht.near[g].size() > 1;
@@ -1517,12 +1630,29 @@ static void factor(Handle& h, int precision, int spd) {
       std::vector<CopyTask> ct;
       std::vector<LuTask> lu;
       GemmBatch ng;
+      std::vector<FoldTask> fk;
+      std::vector<FoldTerm> fkt;
       for (int g = 0; g < nb; ++g) {
         if (!has_lu[g]) continue;
         int dq = diag_q(g);
         void* dst = (char*)LUK + so[g] * ws;
         ct.push_back(CopyTask{Ablk[g][dq].ptr, dst, n[g], n[g], Ablk[g][dq].ld, n[g]});
         lu.push_back(LuTask{dst, n[g], n[g], n[g], pivK + (size_t)g * 256, finfo, 0});
+        if (qr_route) {
+          // R_K: rows of [A_KJ]_J^T = columns of every A_KJ, J != K
+          FoldTask f{};
+          f.R = (double*)((char*)Mk + so[g] * ws);
+          f.n = n[g];
+          f.t0 = (int)fkt.size();
+          for (size_t q = 0; q < ht.near[g].size(); ++q) {
+            int j = ht.near[g][q];
+            if (j == g) continue;
+            fkt.push_back(FoldTerm{(const double*)Ablk[g][q].ptr, n[j], Ablk[g][q].ld, Ablk[g][q].tr});
+          }
+          f.nt = (int)fkt.size() - f.t0;
+          fk.push_back(f);
+          continue;
+        }
         std::vector<GemmTerm> ts;
         for (size_t q = 0; q < ht.near[g].size(); ++q) {
           int j = ht.near[g][q];
@@ -1534,7 +1664,8 @@ static void factor(Handle& h, int precision, int spd) {
       }
       run_copy(W, W, false, ct, maxn, maxn, sc);
       run_getrf(W, lu, sc);
-      ng.run(W, false, true, sc);
+      if (qr_route) run_fold(fk, fkt, pts, h.kp, sc);
+      else ng.run(W, false, true, sc);
     }
     if (W == Prec::F32) {
       // mixed precision: M_K = A_KK^-1 NG_K A_KK^-T through the explicit
@@ -1561,7 +1692,7 @@ static void factor(Handle& h, int precision, int spd) {
       run_trsm(W, false, false, false, tu, maxn, sc);
       x1.run(W, false, false, sc);
       x2.run(W, false, true, sc);
-    } else {
+    } else if (!qr_route) {
       // M_K = A_KK^-1 NG_K A_KK^-T  (NG symmetric): X = A^-1 NG; M = A^-1 X^T
       std::vector<TrsmTask> tl, tu;
       std::vector<CopyTask> tr;
@@ -1586,18 +1717,38 @@ static void factor(Handle& h, int precision, int spd) {
       }
       run_trsm(W, true, true, false, tl2, maxn, sc);
       run_trsm(W, false, false, false, tu2, maxn, sc);
-      // M = Tmp (symmetric up to rounding)
+      std::swap(Mk, Tmp);   // M = Tmp (symmetric up to rounding)
+    } else {
+      // Z_K = A_KK^-1 R_K^T (P L U = A_KK): transpose R_K, then L and U solves
+      std::vector<TrsmTask> tl, tu;
+      std::vector<CopyTask> tr;
+      for (int g = 0; g < nb; ++g) {
+        if (!has_lu[g]) continue;
+        void* L = (char*)LUK + so[g] * ws;
+        void* Z = (char*)Tmp + so[g] * ws;
+        tr.push_back(CopyTask{(char*)Mk + so[g] * ws, Z, n[g], n[g], n[g], n[g]});
+        tl.push_back(TrsmTask{L, Z, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
+        tu.push_back(TrsmTask{L, Z, n[g], n[g], n[g], n[g], nullptr});
+      }
+      run_copy(W, W, true, tr, maxn, maxn, sc);
+      run_trsm(W, true, true, false, tl, maxn, sc);
+      run_trsm(W, false, false, false, tu, maxn, sc);
       std::swap(Mk, Tmp);
     }
-    // Gram of the fill-in block row: sum_K A_IK M_K A_IK^T.  For a chunk of
-    // near positions, every pair's V_IK = op(A_IK) M_K and P_IK = V_IK A_IK^T
-    // go in one launch each; the P_IK are then added into GF one near
-    // position after the other, so the FP32 summation order does not depend
-    // on the chunking.
-    void* GF = sc.alloc(so[nb] * ws, true);
+    // Fill-in block row of every box.  Both routes form V_IK = op(A_IK) X_K
+    // for a chunk of near positions in one launch (X_K = Z_K or M_K).  The
+    // QR route folds the V_IK of a box into its triangle RF one near
+    // position after the other; the Gram route forms P_IK = V_IK A_IK^T and
+    // adds them into GF in near-position order, so that neither result
+    // depends on the chunking.
+    void* GF = qr_route ? nullptr : sc.alloc(so[nb] * ws, true);
+    double* RF = qr_route ? (double*)sc.alloc(NN * 8, true) : nullptr;
+    std::vector<int> has_fill(nb, 0);
     {
       std::vector<PairSlot> prs = near_pairs(ht.near, [&](int g, int K) { return K != g && has_lu[K]; },
-                                             [&](int g, int K) { return ((size_t)n[g] * n[K] + (size_t)n[g] * n[g]) * ws; });
+                                             [&](int g, int K) {
+                                               return ((size_t)n[g] * n[K] + (qr_route ? 0 : (size_t)n[g] * n[g])) * ws;
+                                             });
       std::vector<std::vector<int>> by_box(nb);
       for (size_t p0 = 0; p0 < prs.size();) {
         const size_t p1 = chunk_pairs(prs, p0, pair_budget);
@@ -1607,14 +1758,38 @@ static void factor(Handle& h, int precision, int spd) {
           const PairSlot& pr = prs[q];
           const int g = pr.g, k = pr.k, K = pr.j;
           char* V = Vb + pr.off;
-          char* P = V + (size_t)n[g] * n[K] * ws;
           g1.add1(V, n[g], n[g], n[K], Ablk[g][k].ptr, Ablk[g][k].ld, (char*)Mk + so[K] * ws, n[K], n[K], 1.0, 0.0,
                   nullptr, 0, Ablk[g][k].tr ? 1 : 0);
-          g2.add1(P, n[g], n[g], n[g], V, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K], 1.0, 0.0, nullptr, 0,
-                  Ablk[g][k].tr ? 2 : 0);
+          if (!qr_route) {
+            char* P = V + (size_t)n[g] * n[K] * ws;
+            g2.add1(P, n[g], n[g], n[g], V, n[g], Ablk[g][k].ptr, Ablk[g][k].ld, n[K], 1.0, 0.0, nullptr, 0,
+                    Ablk[g][k].tr ? 2 : 0);
+          }
           by_box[g].push_back((int)q);
+          has_fill[g] = 1;
         }
         g1.run(W, false, false, sc);
+        if (qr_route) {
+          prof_tag("fillin_fold");
+          std::vector<FoldTask> ft;
+          std::vector<FoldTerm> fterms;
+          for (int g = 0; g < nb; ++g) {
+            if (by_box[g].empty()) continue;
+            FoldTask f{};
+            f.R = RF + off[g];
+            f.n = n[g];
+            f.t0 = (int)fterms.size();
+            f.accumulate = 1;
+            for (int q : by_box[g]) fterms.push_back(FoldTerm{(const double*)(Vb + prs[q].off), n[prs[q].j], n[g], 0});
+            f.nt = (int)fterms.size() - f.t0;
+            ft.push_back(f);
+            by_box[g].clear();
+          }
+          run_fold(ft, fterms, pts, h.kp, sc);
+          prof_tag("fillin");
+          p0 = p1;
+          continue;
+        }
         prof_tag("fillin_gram");
         g2.run(W, false, true, sc);
         std::vector<AccumTask> at;
@@ -1628,6 +1803,11 @@ static void factor(Handle& h, int precision, int spd) {
           by_box[g].clear();
           maxe = std::max(maxe, ne);
         }
+        {
+          double by = 0.0;
+          for (const AccumTask& a : at) by += (double)ws * a.n * (a.np + 2.0);
+          prof_note(0.0, by);
+        }
         launch_accum_parts(W, sc.up(at), (int)at.size(), sc.up(parts), maxe, s);
         prof_tag("fillin");
         p0 = p1;
@@ -1635,6 +1815,68 @@ static void factor(Handle& h, int precision, int spd) {
     }
     // ---------------- 2. basis with fill-ins (eq. fillu) ---------------
     prof_tag("basis");
+    double* R = (double*)sc.alloc(NN * 8);
+    int* piv = (int*)sc.alloc((size_t)nb * 256 * 4);
+    int* rank = (int*)sc.alloc((size_t)nb * 4);
+    int* cinfo = (int*)sc.alloc(8, true);   // [0] basis matrix non-finite, [1] fill-in LU zero pivot
+    // far-field samples of every box (candidates in point form)
+    std::vector<int> cand_all, samp_all;
+    std::vector<size_t> co(nb + 1, 0), sof(nb + 1, 0);
+    for (int g = 0; g < nb; ++g) {
+      const BoxRef& b = ht.ref[g];
+      const Problem& pb = h.probs[b.prob];
+      far_samples(pb.t, b.level, b.local, h.opt.far_s0, h.opt.far_smin, samp);
+      for (int64_t q : samp) samp_all.push_back((int)(pb.off + q));
+      sof[g + 1] = samp_all.size();
+      cand_all.insert(cand_all.end(), ht.cand[g].begin(), ht.cand[g].end());
+      co[g + 1] = cand_all.size();
+    }
+    int* dc = sc.up(cand_all);
+    int* ds = sc.up(samp_all);
+    const double tol_basis = (W == Prec::F64) ? h.opt.tol : std::max(h.opt.tol, 1.0 / 1024.0);
+    h.tol_basis = tol_basis;
+    h.basis_route = qr_route ? "qr" : "gram";
+    if (qr_route) {
+      // point form of the fill-in rows: B_pt = T^-1 B_lev, and B_lev B_lev^T
+      // = RF^T RF, so Y = T^-1 RF^T stands for them; fold [Y^T; far-field
+      // rows] and take the pivoted QR of the triangle (at the leaves T = I
+      // and the samples fold straight into RF)
+      double* Rpt = RF;
+      std::vector<FoldTask> ft;
+      std::vector<FoldTerm> fterms;
+      if (H > 0) {
+        double* Y = (double*)sc.alloc(NN * 8);
+        Rpt = (double*)sc.alloc(NN * 8);
+        std::vector<CopyTask> tr;
+        std::vector<TrsmTask> tt;
+        for (int g = 0; g < nb; ++g) {
+          if (!has_fill[g]) continue;
+          tr.push_back(CopyTask{RF + off[g], Y + off[g], n[g], n[g], n[g], n[g]});
+          tt.push_back(TrsmTask{Tcur->as<double>() + t_off[g], Y + off[g], n[g], n[g], n[g], n[g], nullptr});
+        }
+        run_copy(Prec::F64, Prec::F64, true, tr, maxn, maxn, sc);
+        run_trsm(Prec::F64, false, false, false, tt, maxn, sc);
+        for (int g = 0; g < nb; ++g) {
+          FoldTask f{dc + co[g], ds + sof[g], Rpt + off[g], n[g], (int)(sof[g + 1] - sof[g]), (int)fterms.size(), 0, 0};
+          if (has_fill[g]) {
+            fterms.push_back(FoldTerm{Y + off[g], n[g], n[g], 0});
+            f.nt = 1;
+          }
+          ft.push_back(f);
+        }
+      } else {
+        for (int g = 0; g < nb; ++g) {
+          const int m_s = (int)(sof[g + 1] - sof[g]);
+          if (m_s > 0) ft.push_back(FoldTask{dc + co[g], ds + sof[g], RF + off[g], n[g], m_s, 0, 0, 1});
+        }
+      }
+      run_fold(ft, fterms, pts, h.kp, sc);
+      std::vector<PqrTask> qt;
+      for (int g = 0; g < nb; ++g)
+        qt.push_back(PqrTask{Rpt + off[g], n[g], n[g], n[g], piv + (size_t)g * 256, R + off[g], rank + g, tol_basis,
+                             h.opt.max_rank, cinfo});
+      run_pqr(qt, sc);
+    } else {
     double* G = (double*)sc.alloc(NN * 8);
     {
       std::vector<CopyTask> ct;
@@ -1656,19 +1898,6 @@ static void factor(Handle& h, int precision, int spd) {
         G = G2;
       }
       // far-field block row Gram K(cand, samples) K(cand, samples)^T
-      std::vector<int> cand_all, samp_all;
-      std::vector<size_t> co(nb + 1, 0), sof(nb + 1, 0);
-      for (int g = 0; g < nb; ++g) {
-        const BoxRef& b = ht.ref[g];
-        const Problem& pb = h.probs[b.prob];
-        far_samples(pb.t, b.level, b.local, h.opt.far_s0, h.opt.far_smin, samp);
-        for (int64_t q : samp) samp_all.push_back((int)(pb.off + q));
-        sof[g + 1] = samp_all.size();
-        cand_all.insert(cand_all.end(), ht.cand[g].begin(), ht.cand[g].end());
-        co[g + 1] = cand_all.size();
-      }
-      int* dc = sc.up(cand_all);
-      int* ds = sc.up(samp_all);
       std::vector<KgramTask> kt;
       for (int g = 0; g < nb; ++g) {
         int m = (int)(sof[g + 1] - sof[g]);
@@ -1677,19 +1906,13 @@ static void factor(Handle& h, int precision, int spd) {
       }
       run_kgram(W, kt, maxn, pts, h.kp, sc);
     }
-    double* R = (double*)sc.alloc(NN * 8);
-    int* piv = (int*)sc.alloc((size_t)nb * 256 * 4);
-    int* rank = (int*)sc.alloc((size_t)nb * 4);
-    int* cinfo = (int*)sc.alloc(8, true);   // [0] basis Gram non-finite, [1] fill-in LU zero pivot
-    H2_CUDA(cudaMemcpyAsync(cinfo + 1, finfo, 4, cudaMemcpyDeviceToDevice, s));
     {
-      // Rank tolerance of the fill-in basis.  In mixed precision the Gram
+      // Rank tolerance of the Gram route.  In mixed precision the Gram
       // matrix is accumulated in FP32, which resolves the block row only to
       // about 2^-10 of its norm; pivoting below that would select skeletons
-      // from rounding noise (and grow the interpolation coefficients level by
-      // level), so the threshold is floored there.  The FP64 refinement
-      // against the H^2 operator recovers the accuracy.
-      const double tol_basis = (W == Prec::F32) ? std::max(h.opt.tol, 1.0 / 1024.0) : h.opt.tol;
+      // from rounding noise (and grow the interpolation coefficients level
+      // by level), so the threshold is floored there (tol_basis above).  The
+      // FP64 refinement against the H^2 operator recovers the accuracy.
       std::vector<CholTask> ct;
       double* Lch = (double*)sc.alloc(NN * 8);
       for (int g = 0; g < nb; ++g)
@@ -1697,13 +1920,25 @@ static void factor(Handle& h, int precision, int spd) {
                               h.opt.max_rank, cinfo, Lch + off[g]});
       run_pchol(ct, sc);
     }
+    }
+    H2_CUDA(cudaMemcpyAsync(cinfo + 1, finfo, 4, cudaMemcpyDeviceToDevice, s));
     std::vector<int> hr(nb), hpiv((size_t)nb * 256);
     int hci[2] = {0, 0};
     H2_CUDA(cudaMemcpyAsync(hr.data(), rank, nb * 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaMemcpyAsync(hpiv.data(), piv, hpiv.size() * 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaMemcpyAsync(hci, cinfo, 8, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaStreamSynchronize(s));
-    if (hci[0]) throw StatusError(H2_ERR_NONFINITE, "non-finite value in a basis Gram matrix");
+    {
+      // rank-dependent work of the pivoted Cholesky / pivoted QR just run
+      double f = 0.0;
+      for (int g = 0; g < nb; ++g) {
+        const double nn = n[g], rr = std::min(hr[g], n[g]);
+        f += qr_route ? 4.0 * nn * nn * rr - 4.0 * nn * rr * rr + 4.0 * rr * rr * rr / 3.0
+                      : nn * rr * rr - 2.0 * rr * rr * rr / 3.0;
+      }
+      prof_add(qr_route ? "pqr_f64" : "pchol_f64", f);
+    }
+    if (hci[0]) throw StatusError(H2_ERR_NONFINITE, "non-finite value in a basis block row");
     if (hci[1]) throw StatusError(H2_ERR_SINGULAR, "zero or non-finite pivot in a diagonal-block LU (fill-ins)");
     ht.r.resize(nb);
     ht.sk.resize(nb);
@@ -2361,6 +2596,7 @@ static void construct_impl(h2_handle_* H, int P, const double* const* points, co
   check_opts(kern, opt);
   Handle& h = H->h;
   h.s = (cudaStream_t)stream;
+  H2_CUDA(cudaGetDevice(&h.dev));
   h.kp = KParams{kern->kind, kern->delta, kern->kappa, kern->ell, kern->nugget};
   h.opt = *opt;
   double t0 = now_ms();
@@ -2796,11 +3032,23 @@ h2_status h2_logdet_noalloc(h2_handle H, double* log_abs_det, int32_t* sign) {
   }
   return guard([&] {
     Handle& h = H->h;
-    int dev = 0;
-    H2_CUDA(cudaGetDevice(&dev));
+    // The scratch array used is the one on the handle's device (where its
+    // factors and stream live), made current for the duration of the call
+    // when the caller's current device is another one.
+    const int dev = h.dev;
     if (dev < 0 || dev >= 256) throw StatusError(H2_ERR_ARG, "device index out of range");
+    int cur = 0;
+    H2_CUDA(cudaGetDevice(&cur));
+    struct Restore {
+      int prev, now;
+      ~Restore() {
+        if (prev != now) (void)cudaSetDevice(prev);
+      }
+    } restore{cur, dev};
+    if (cur != dev) H2_CUDA(cudaSetDevice(dev));
     if (!g_noalloc_ptr[dev]) {
       // first call on this device: resolve the scratch array's device address
+      // (the host-side name is only a stand-in), with that device current
       void* p = nullptr;
       H2_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
       g_noalloc_ptr[dev] = p;
@@ -2852,7 +3100,9 @@ h2_status h2_stats(h2_handle H, char* json, size_t cap) {
     Handle& h = H->h;
     std::ostringstream o;
     o << "{\"N\":" << h.Ntot << ",\"problems\":" << h.probs.size() << ",\"heights\":" << h.Hmax
-      << ",\"construct_ms\":" << h.t_construct_ms << ",\"factor_ms\":" << h.t_factor_ms << ",\"levels\":[";
+      << ",\"construct_ms\":" << h.t_construct_ms << ",\"factor_ms\":" << h.t_factor_ms
+      << ",\"basis_route\":\"" << (h.factored ? h.basis_route : "none")
+      << "\",\"tol_basis\":" << h.tol_basis << ",\"levels\":[";
     for (int H2i = 0; H2i < h.Hmax; ++H2i) {
       const Height& ht = h.hs[H2i];
       double rs = 0, rmax = 0, ro = 0, nearc = 0, farc = 0;

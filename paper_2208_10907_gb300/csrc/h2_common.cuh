@@ -144,6 +144,7 @@ struct PqrTask {       // Householder QR with column pivoting of an m x n matrix
   int* rank;
   double tol;
   int max_rank;
+  int* info;           // set to 1 if a non-finite column norm is met (may be null)
 };
 
 struct HqrTask {       // QR of M (n x r): Q = [U^R U^S] (n x n), W (r x r)
@@ -154,11 +155,17 @@ struct HqrTask {       // QR of M (n x r): Q = [U^R U^S] (n x n), W (r x r)
   int n, r;
 };
 
-struct FoldTask {      // R0 (n x n upper) of K(cand, samples)^T, streamed
-  const int* cand;     // n point indices
+struct FoldTerm {      // explicit rows of B^T: row q (< rows), element j (< n)
+  const double* X;     // tr = 0: X[j + q ld] (rows are columns of X); tr = 1: X[q + j ld]
+  int rows, ld, tr;
+};
+struct FoldTask {      // R (n x n upper) <- triangle of [R; rows of the terms; K(cand, samples)^T]
+  const int* cand;     // n point indices (read when m > 0)
   const int* samp;     // m point indices
-  double* R;           // n x n, ld n (output)
+  double* R;           // n x n, ld n
   int n, m;
+  int t0, nt;          // explicit-row terms [t0, t0 + nt), folded first
+  int accumulate;      // 0: start from R = 0; 1: continue from the R in memory
 };
 
 struct KgramTask {     // G (+)= K(cand, samp) K(cand, samp)^T
@@ -223,7 +230,7 @@ void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, 
 void launch_pchol(const CholTask* d, int ntasks, cudaStream_t s);
 void launch_pqr(const PqrTask* d, int ntasks, cudaStream_t s);
 void launch_hqr(Prec p, const HqrTask* d, int ntasks, cudaStream_t s);
-void launch_fold(const FoldTask* d, int ntasks, Points pts, KParams kp, cudaStream_t s);
+void launch_fold(const FoldTask* d, int ntasks, const FoldTerm* terms, Points pts, KParams kp, cudaStream_t s);
 void launch_kgram(Prec p, const KgramTask* d, int ntasks, int maxn, Points pts, KParams kp,
                   cudaStream_t s);
 void launch_assemble(Prec p, const AsmTask* d, int ntasks, int maxr, int maxc, Points pts,

@@ -14,6 +14,13 @@ void prof_note(double flops, double bytes) {
 
 void prof_tag(const char* tag) { prof().tag = tag ? tag : ""; }
 
+void prof_add(const char* base, double flops) {
+  std::string name(base);
+  if (!prof().tag.empty()) name += "@" + prof().tag;
+  auto it = prof().stats.find(name);
+  if (it != prof().stats.end()) it->second.flops += flops;
+}
+
 void Prof::resolve() {
   for (auto& q : pending) {
     float ms = 0.f;

@@ -34,6 +34,9 @@ struct Prof {
 Prof& prof();
 void prof_note(double flops, double bytes);
 void prof_tag(const char* tag);   // nullptr clears
+// Add flops to the statistics of kernel `base` under the current tag (work
+// known only after the launch, e.g. rank-dependent).
+void prof_add(const char* base, double flops);
 
 struct ProfScope {
   std::string name;

@@ -380,7 +380,8 @@ __global__ void __launch_bounds__(NT) pqr_kernel(const PqrTask* __restrict__ tas
     double pv;
     int p;
     block_argmax(best, bi, s_val, s_idx, pv, p);
-    if (p < k || p >= n) {   // NaN column norms: stop here
+    if (p < k || p >= n || pv == INFINITY) {   // non-finite column norms: stop here, flag it
+      if (threadIdx.x == 0 && tk.info) *tk.info = 1;
       rank = k;
       break;
     }
@@ -550,32 +551,192 @@ __global__ void __launch_bounds__(NT) hqr_kernel(const HqrTask* __restrict__ tas
 }
 
 // ---------------------------------------------------------------------------
-// Streamed fold of a far-field block row: R0 (n x n, upper) with
-// R0^T R0 = B B^T for B = K(x[cand], x[samp]) (n x m), by Householder
-// elimination of 32-sample chunks of B^T against the running triangle.
-// The chunk is evaluated straight into shared memory; B is never stored.
+// Streamed fold of a block row B (n x cols): R (n x n, upper) with
+// R^T R = B B^T, by Householder elimination of 32-row chunks of B^T against
+// the running triangle (the pivoted QR of R then has the pivots and R of the
+// pivoted QR of B^T, eq. u / eq. fillu).  The rows of B^T come from explicit
+// blocks (FoldTerm: the fill-in products, near blocks, a transformed
+// triangle) and then from the far-field samples, whose kernel values are
+// evaluated straight into shared memory (never stored).
 // ---------------------------------------------------------------------------
-constexpr int FC = 32;
+constexpr int FC = 32;      // rows per chunk (one per lane of a warp)
+constexpr int FNB = 16;     // panel width of the blocked elimination
+constexpr int FLD = 257;    // leading dimension of the shared row tiles
 
-__global__ void __launch_bounds__(NT) fold_kernel(const FoldTask* __restrict__ tasks, Points pts,
-                                                  KParams kp) {
+// Shared state of one fold CTA.
+struct FoldSmem {
+  double C[FC][FLD];        // the chunk of rows being folded (zero-padded to FC rows)
+  double Rp[FNB][FLD];      // R rows [k0, k0 + nb) of the current panel, columns k0 ..
+  double V[FC][FNB];        // Householder vectors of the panel (C part; the R part is e_k)
+  double T[FNB][FNB];       // block reflector: H_0 ... H_{nb-1} = I - Y T Y^T (upper)
+  double tau[FNB];
+  double scol[FNB];
+  double cx[256], cy[256], cz[256];
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fold the chunk S.C (FC x n) into R (n x n upper, global, ld n): the QR of
+// [R; C] by panels of FNB columns.  In a panel, reflector k (acting on R row
+// k and the chunk rows) annihilates column k of C and is applied at once to
+// the panel's other columns (one warp per column); the panel's reflectors
+// are then accumulated into the compact form I - Y T Y^T and applied to the
+// trailing columns together (W = R_p + V^T C, W <- T^T W, R_p -= W,
+// C -= V W), one column per thread with W in registers.
+__device__ void fold_chunk(double* __restrict__ R, int n, FoldSmem& S) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
+  for (int k0 = 0; k0 < n; k0 += FNB) {
+    const int nb = min(FNB, n - k0), w0 = n - k0;
+    // panel rows of R into shared memory (column by column, coalesced)
+    for (int e = tid; e < nb * w0; e += NT) {
+      const int i = e % nb, jj = e / nb;
+      S.Rp[i][jj] = R[(long long)(k0 + i) + (long long)(k0 + jj) * n];
+    }
+    for (int e = tid; e < FC * FNB; e += NT) S.V[e / FNB][e % FNB] = 0.0;
+    __syncthreads();
+    // panel factorization
+    for (int kk = 0; kk < nb; ++kk) {
+      const int k = k0 + kk;
+      if (warp == 0) {
+        const double x = S.C[lane][k];
+        const double sq = warp_sum(x * x);
+        const double r = S.Rp[kk][kk];
+        double v = 0.0, t = 0.0, beta = r;
+        if (sq != 0.0) {
+          const double alpha = sqrt(r * r + sq);
+          beta = r >= 0.0 ? -alpha : alpha;
+          const double v0 = r - beta;
+          v = x / v0;
+          t = -v0 / beta;
+        }
+        S.V[lane][kk] = v;
+        if (lane == 0) {
+          S.tau[kk] = t;
+          S.Rp[kk][kk] = beta;
+        }
+      }
+      __syncthreads();
+      const double t = S.tau[kk];
+      if (t != 0.0) {
+        for (int jj = kk + 1 + warp; jj < nb; jj += nwarp) {
+          const double vq = S.V[lane][kk];
+          const double c = S.C[lane][k0 + jj];
+          const double w = t * (S.Rp[kk][jj] + warp_sum(vq * c));
+          S.C[lane][k0 + jj] = c - vq * w;
+          __syncwarp();
+          if (lane == 0) S.Rp[kk][jj] -= w;
+        }
+      }
+      __syncthreads();
+    }
+    // T of the panel (one warp): T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) (V^T v_i)
+    if (warp == 0) {
+      for (int i = 0; i < FNB; ++i) {
+        double sv = 0.0;
+        if (lane < i && i < nb)
+          for (int q = 0; q < FC; ++q) sv += S.V[q][lane] * S.V[q][i];
+        if (lane < FNB) S.scol[lane] = sv;
+        __syncwarp();
+        const double ti = (i < nb) ? S.tau[i] : 0.0;
+        if (lane < i) {
+          double acc = 0.0;
+          for (int l = lane; l < i; ++l) acc += S.T[lane][l] * S.scol[l];
+          S.T[lane][i] = -ti * acc;
+        } else if (lane < FNB) {
+          S.T[lane][i] = (lane == i) ? ti : 0.0;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // ---- trailing columns j >= k0 + nb: one column per thread
+    {
+      const int jj = nb + tid;
+      if (jj < w0) {
+        double w[FNB];
+#pragma unroll
+        for (int i = 0; i < FNB; ++i) w[i] = (i < nb) ? S.Rp[i][jj] : 0.0;
+#pragma unroll 8
+        for (int q = 0; q < FC; ++q) {
+          const double cq = S.C[q][k0 + jj];
+#pragma unroll
+          for (int i = 0; i < FNB; ++i) w[i] = fma(S.V[q][i], cq, w[i]);
+        }
+        // w <- T^T w, in place from the last entry down
+#pragma unroll
+        for (int i = FNB - 1; i >= 0; --i) {
+          double a = 0.0;
+#pragma unroll
+          for (int p = 0; p <= i; ++p) a = fma(S.T[p][i], w[p], a);
+          w[i] = a;
+        }
+#pragma unroll
+        for (int i = 0; i < FNB; ++i)
+          if (i < nb) S.Rp[i][jj] -= w[i];
+        for (int q0 = 0; q0 < FC; q0 += 8) {   // eight independent chunk rows at a time
+          double c[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) c[q] = S.C[q0 + q][k0 + jj];
+#pragma unroll
+          for (int i = 0; i < FNB; ++i)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c[q] = fma(-S.V[q0 + q][i], w[i], c[q]);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) S.C[q0 + q][k0 + jj] = c[q];
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * w0; e += NT) {
+      const int i = e % nb, jj = e / nb;
+      R[(long long)(k0 + i) + (long long)(k0 + jj) * n] = S.Rp[i][jj];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(NT, 2) fold_kernel(const FoldTask* __restrict__ tasks,
+                                                     const FoldTerm* __restrict__ terms, Points pts, KParams kp) {
   const FoldTask tk = tasks[blockIdx.x];
   const int n = tk.n;
   double* R = tk.R;
-  extern __shared__ double fold_smem[];
-  double (*C)[257] = reinterpret_cast<double (*)[257]>(fold_smem);   // FC x 257
-  __shared__ double vs[FC + 1];
-  __shared__ double s_tau, s_beta;
-  __shared__ double cx[256], cy[256], cz[256];
-  __shared__ int s_skip;
-  for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) {
-    int g = tk.cand[i];
-    cx[i] = pts.x[g];
-    cy[i] = pts.y[g];
-    cz[i] = pts.z[g];
-  }
+  extern __shared__ __align__(16) unsigned char fold_raw[];
+  FoldSmem& S = *reinterpret_cast<FoldSmem*>(fold_raw);
+  if (!tk.accumulate)
+    for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
+  if (tk.m > 0)
+    for (int i = threadIdx.x; i < n; i += NT) {
+      int g = tk.cand[i];
+      S.cx[i] = pts.x[g];
+      S.cy[i] = pts.y[g];
+      S.cz[i] = pts.z[g];
+    }
   __syncthreads();
+  // explicit rows: row q of a term, element j = tr ? X[q + j ld] : X[j + q ld]
+  for (int t = tk.t0; t < tk.t0 + tk.nt; ++t) {
+    const FoldTerm ft = terms[t];
+    for (int q0 = 0; q0 < ft.rows; q0 += FC) {
+      const int c = min(FC, ft.rows - q0);
+      if (ft.tr) {   // the chunk's rows are columns of X: threads along q read contiguously
+        for (int e = threadIdx.x; e < FC * n; e += NT) {
+          const int q = e % FC, j = e / FC;
+          S.C[q][j] = q < c ? ft.X[(long long)(q0 + q) + (long long)j * ft.ld] : 0.0;
+        }
+      } else {
+        for (int e = threadIdx.x; e < FC * n; e += NT) {
+          const int q = e / n, j = e % n;
+          S.C[q][j] = q < c ? ft.X[(long long)j + (long long)(q0 + q) * ft.ld] : 0.0;
+        }
+      }
+      __syncthreads();
+      fold_chunk(R, n, S);
+    }
+  }
+  // far-field samples: row q = K(x[samp[q]], x[cand[:]])
   for (int s0 = 0; s0 < tk.m; s0 += FC) {
     const int c = min(FC, tk.m - s0);
     for (int e = threadIdx.x; e < FC * n; e += NT) {
@@ -583,51 +744,12 @@ __global__ void __launch_bounds__(NT) fold_kernel(const FoldTask* __restrict__ t
       double v = 0.0;
       if (q < c) {
         int g = tk.samp[s0 + q];
-        v = kernel_eval(kp, cx[j] - pts.x[g], cy[j] - pts.y[g], cz[j] - pts.z[g]);
+        v = kernel_eval(kp, S.cx[j] - pts.x[g], S.cy[j] - pts.y[g], S.cz[j] - pts.z[g]);
       }
-      C[q][j] = v;
+      S.C[q][j] = v;
     }
     __syncthreads();
-    for (int k = 0; k < n; ++k) {
-      if (threadIdx.x < 32) {
-        double rkk = R[k + (long long)k * n];
-        double x = threadIdx.x < FC ? C[threadIdx.x][k] : 0.0;
-        double s = x * x;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        s = __shfl_sync(0xffffffffu, s, 0);
-        if (threadIdx.x == 0) {
-          if (s == 0.0) {
-            s_skip = 1;
-          } else {
-            double alpha = sqrt(rkk * rkk + s);
-            double beta = rkk >= 0.0 ? -alpha : alpha;
-            double v0 = rkk - beta;
-            s_tau = 2.0 / (v0 * v0 + s);
-            s_beta = beta;
-            vs[0] = v0;
-            s_skip = 0;
-          }
-        }
-        if (threadIdx.x < FC) vs[threadIdx.x + 1] = x;
-      }
-      __syncthreads();
-      if (!s_skip) {
-        const double tau = s_tau;
-        for (int j = k + 1 + threadIdx.x; j < n; j += NT) {
-          double rkj = R[k + (long long)j * n];
-          double w = vs[0] * rkj;
-#pragma unroll 8
-          for (int q = 0; q < FC; ++q) w += vs[q + 1] * C[q][j];
-          w *= tau;
-          R[k + (long long)j * n] = rkj - vs[0] * w;
-#pragma unroll 8
-          for (int q = 0; q < FC; ++q) C[q][j] -= vs[q + 1] * w;
-        }
-        if (threadIdx.x == 0) R[k + (long long)k * n] = s_beta;
-      }
-      __syncthreads();
-    }
+    fold_chunk(R, n, S);
   }
 }
 
@@ -988,12 +1110,13 @@ void launch_hqr(Prec p, const HqrTask* d, int ntasks, cudaStream_t s) {
   H2_LAUNCH_CHECK();
 }
 
-void launch_fold(const FoldTask* d, int ntasks, Points pts, KParams kp, cudaStream_t s) {
+void launch_fold(const FoldTask* d, int ntasks, const FoldTerm* terms, Points pts, KParams kp, cudaStream_t s) {
   if (ntasks <= 0) return;
   ProfScope ps("fold_f64", s);
-  size_t smem = (size_t)FC * 257 * sizeof(double);
+  size_t smem = sizeof(FoldSmem);
   H2_CUDA(cudaFuncSetAttribute(fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fold_kernel<<<ntasks, NT, smem, s>>>(d, pts, kp);
+  H2_CUDA(cudaFuncSetAttribute(fold_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  fold_kernel<<<ntasks, NT, smem, s>>>(d, terms, pts, kp);
   H2_LAUNCH_CHECK();
 }
 

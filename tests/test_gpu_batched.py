@@ -53,9 +53,19 @@ def test_batched_matches_oracle_and_single(precision):
         ldb, sgb = H.h2_logdet(hb, len(Xs))
         for p, X in enumerate(Xs):
             pb = O.Problem(X, "laplace", 128, 1.0, 1e-8, 100)
-            xo, _, _ = O.refine(O.H2Operator(pb), O.ULVFactor(pb), B[off[p]:off[p + 1]], 1e-10, 40)
+            fac = O.ULVFactor(pb)
+            xo, _, _ = O.refine(O.H2Operator(pb), fac, B[off[p]:off[p + 1]], 1e-10, 40)
             xg = Xc.T[off[p]:off[p + 1]]
             assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+            # log-det against the oracle: FP64 the same route (1e-9); mixed
+            # the oracle's Gram route at the effective tolerance, N 2^-17
+            # (each of the N pivots within 2^7 FP32 unit roundoffs)
+            if precision == H.H2_FP64:
+                lo, so = fac.logdet()
+                assert sgb[p] == so and abs(ldb[p] - lo) <= 1e-9 * abs(lo), (p, ldb[p], lo)
+            else:
+                lo, so = O.ULVFactor(pb, route="gram", tol_basis=2.0 ** -10).logdet()
+                assert sgb[p] == so and abs(ldb[p] - lo) <= len(X) * 2.0 ** -17, (p, ldb[p], lo)
             # the same problem alone
             h1 = H.h2_construct(torch.from_numpy(X).cuda(), len(X), kern, opt)
             try:

@@ -182,13 +182,9 @@ def test_hss_special_case_weak_admissibility():
     """eta -> infinity on a line: distinct boxes are far from the first level
     below the root on (weak admissibility), there are no fill-ins, and the
     method reduces to the paper's HSS-ULV (Sec. II-C).  Exact far-field block
-    rows (far_s0 = 0).  The FP64 refined solution matches the oracle's.  The
-    log-det is that of the factored approximation: its basis comes from the
-    Gram matrix B B^T, whose pivoted Cholesky resolves the block row only to
-    about sqrt(eps) = 1.5e-8 of its norm (below tol = 1e-10 here), so the
-    factored matrix is within about 3e-8 ||A|| of A and
-    |log det - log det A| <= N cond(A) 3e-8 against the dense log-det (the
-    oracle's own value moves by 1e-2 between CPU platforms for this case)."""
+    rows (far_s0 = 0), tol 1e-10.  The FP64 factorization's log-det and its
+    unrefined solution match the oracle's (and dense LU, which the oracle
+    matches to rounding here); the refined solution matches too."""
     X = synth.line(1024, 5)
     N = len(X)
     pb = O.Problem(X, "laplace", 64, 1e12, 1e-10, 128, s0=0)
@@ -203,13 +199,48 @@ def test_hss_special_case_weak_admissibility():
         H.h2_factor(h, H.H2_FP64)
         bt = torch.from_numpy(b).cuda()
         xt = torch.zeros_like(bt)
+        st, ach, it = H.h2_solve(h, bt, xt, 1, N, 1e300, 0)      # unrefined ULV solve
+        assert st == H.H2_OK and it == 0
+        x0 = fac.solve(b)
+        assert np.linalg.norm(xt.cpu().numpy() - x0) / np.linalg.norm(x0) <= 1e-8
         st, ach, it = H.h2_solve(h, bt, xt, 1, N, 1e-10, 30)
         assert st == H.H2_OK and ach[0] <= 1e-10, (st, ach, it)
         assert np.linalg.norm(xt.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
         ld, sg = H.h2_logdet(h)
-        A = O.kernel_matrix("laplace", X, X)
-        so, lo = np.linalg.slogdet(A)
-        bound = N * np.linalg.cond(A) * 3e-8
-        assert sg[0] == so and abs(ld[0] - lo) <= bound, (ld[0], lo, bound)
+        lo, so = fac.logdet()
+        assert sg[0] == so and abs(ld[0] - lo) <= 1e-9 * abs(lo), (ld[0], lo)
+        sd, ldd = np.linalg.slogdet(O.kernel_matrix("laplace", X, X))
+        assert sd == sg[0] and abs(ld[0] - ldd) <= 1e-9 * abs(ldd), (ld[0], ldd)
+    finally:
+        H.h2_destroy(h)
+
+
+def test_blr2_special_case_one_level():
+    """One level (L = 1): the two halves of a line are far from each other,
+    so the method is the paper's BLR^2-ULV (Sec. II-B, eq. lu ... eq.
+    BLR2final): one basis, one partial LU per box (n = 256), and the dense
+    LU of the merged skeletons.  Log-det and unrefined solution against the
+    oracle (which matches dense LU here)."""
+    X = synth.line(512, 13)
+    N = len(X)
+    pb = O.Problem(X, "yukawa", 256, 1e12, 1e-10, 128, s0=0)
+    assert pb.L == 1 and pb.ltop == 0
+    fac = O.ULVFactor(pb)
+    b = synth.rhs(N, 1, 10)[:, 0].copy()
+    pts = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    h = H.h2_construct(pts, N, H.make_kernel("yukawa"),
+                       H.make_options(eta=1e12, leaf=256, tol=1e-10, max_rank=128, far_s0=0, far_smin=1))
+    try:
+        H.h2_factor(h, H.H2_FP64)
+        F, R = H.h2_box_features(h, 0, with_ranks=True)
+        assert R.tolist() == fac.rank_log[0][1]
+        ld, sg = H.h2_logdet(h)
+        lo, so = fac.logdet()
+        assert sg[0] == so and abs(ld[0] - lo) <= 1e-9 * abs(lo), (ld[0], lo)
+        bt = torch.from_numpy(b).cuda()
+        xt = torch.zeros_like(bt)
+        st, ach, it = H.h2_solve(h, bt, xt, 1, N, 1e300, 0)
+        x0 = fac.solve(b)
+        assert st == H.H2_OK and np.linalg.norm(xt.cpu().numpy() - x0) / np.linalg.norm(x0) <= 1e-8
     finally:
         H.h2_destroy(h)

@@ -42,3 +42,28 @@ def test_logdet_noalloc_matches_logdet_twice():
         assert free_after == free_before
     finally:
         H.h2_destroy(h)
+
+
+@pytest.mark.parametrize("spd", [0, 1])
+def test_logdet_noalloc_batched_handle(spd):
+    """A batched handle (three problems of different depths): every
+    problem's value and sign, through the per-problem accumulation of the
+    allocation-free path, equal h2_logdet's; LU (spd = 0) and the Cholesky
+    form (spd = 1) of the Matern-3/2 covariance kernel.  No device memory
+    is allocated by the second call."""
+    Xs = [synth.cube(n, 60 + k) for k, n in enumerate([1500, 700, 2600])]
+    hb = H.h2_construct_batched([torch.from_numpy(X).cuda() for X in Xs], H.make_kernel("matern32"),
+                                H.make_options(leaf=128, tol=1e-10, max_rank=128))
+    try:
+        H.h2_factor(hb, H.H2_FP64, spd)
+        ref, ref_sign = H.h2_logdet(hb, len(Xs))
+        v1, s1 = H.h2_logdet_noalloc(hb, len(Xs))
+        free_before = _free_bytes()
+        v2, s2 = H.h2_logdet_noalloc(hb, len(Xs))
+        free_after = _free_bytes()
+        for v, s in ((v1, s1), (v2, s2)):
+            assert list(s) == list(ref_sign)
+            np.testing.assert_allclose(v, ref, rtol=1e-12, atol=0)
+        assert free_after == free_before
+    finally:
+        H.h2_destroy(hb)
