@@ -159,6 +159,46 @@ static void ensure(DBufP& b, size_t bytes) {
   b = std::make_shared<DBuf>(bytes);
 }
 
+// Pinned host staging for task-array uploads, one ring per stream: a copy
+// from pageable memory would make the host wait for the stream, so task
+// arrays are first copied into pinned memory and uploaded asynchronously,
+// and the host builds the next launch's tasks while the GPU works.  When the
+// ring is full, the stream is synchronised (every earlier upload from it has
+// then completed) and the ring starts over.
+struct PinnedRing {
+  char* buf = nullptr;
+  size_t cap = 0, pos = 0;
+  ~PinnedRing() {
+    if (buf) cudaFreeHost(buf);
+  }
+  void* stage(const void* src, size_t n, cudaStream_t s) {
+    const size_t need = (n + 255) & ~size_t(255);
+    if (need > cap) {
+      H2_CUDA(cudaStreamSynchronize(s));
+      if (buf) cudaFreeHost(buf);
+      buf = nullptr;
+      cap = std::max(need, size_t(64) << 20);
+      H2_CUDA(cudaHostAlloc((void**)&buf, cap, cudaHostAllocDefault));
+      pos = 0;
+    } else if (pos + need > cap) {
+      H2_CUDA(cudaStreamSynchronize(s));
+      pos = 0;
+    }
+    void* p = buf + pos;
+    std::memcpy(p, src, n);
+    pos += need;
+    return p;
+  }
+};
+static void* pinned_stage(const void* src, size_t n, cudaStream_t s) {
+  static std::mutex mu;
+  static std::map<cudaStream_t, std::unique_ptr<PinnedRing>> rings;
+  std::lock_guard<std::mutex> lk(mu);
+  auto& r = rings[s];
+  if (!r) r.reset(new PinnedRing());
+  return r->stage(src, n, s);
+}
+
 // Stream-ordered scratch: everything lives until the Scratch is destroyed.
 // Task lists and small buffers are carved from 32 MB arenas (one device
 // allocation per arena instead of one per launch); large buffers get their
@@ -203,7 +243,7 @@ struct Scratch {
     const size_t nb = v.size() * sizeof(T);
     void* p;
     p = nb <= SMALL ? carve(nb) : fresh(nb)->p;
-    H2_CUDA(cudaMemcpyAsync(p, v.data(), nb, cudaMemcpyHostToDevice, s));
+    H2_CUDA(cudaMemcpyAsync(p, pinned_stage(v.data(), nb, s), nb, cudaMemcpyHostToDevice, s));
     return reinterpret_cast<T*>(p);
   }
   void* alloc(size_t bytes, bool zero = false) {
@@ -1295,7 +1335,9 @@ static PlanP build_matvec_plan(Handle& h, const double* x, double* y, int nrhs) 
 // column-major): LU, log-determinant and the explicit inverse (FP64 in
 // rt.inv, FP64 copy of the factors in rt.LU).  Mixed precision runs it in
 // FP32 on the tensor-core GEMM: the root only preconditions there.
-static void root_factor(Handle& h, Root& rt, int spd, Prec P, void* Aw) {
+// The zero-pivot flag goes to `info` and log|det|, sign to `dlog` (device);
+// the caller reads both once the whole factorization has been issued.
+static void root_factor(Handle& h, Root& rt, int spd, Prec P, void* Aw, int* info, double* dlog) {
   cudaStream_t s = h.s;
   const int n = rt.n;
   if (n == 0) return;
@@ -1304,7 +1346,6 @@ static void root_factor(Handle& h, Root& rt, int spd, Prec P, void* Aw) {
   const size_t es = esz(P);
   auto at = [&](void* base, size_t i, size_t j) -> char* { return (char*)base + (i + j * (size_t)n) * es; };
   int* piv = rt.piv->as<int>();
-  int* info = (int*)sc.alloc(4, true);
   // Blocked right-looking LU with pivoting inside each 64 x 64 diagonal
   // block: the panel factorization touches only that block (one CTA, L2
   // resident), and L21 = A21 U11^-1, U12 = L11^-1 A12 and the trailing
@@ -1312,17 +1353,13 @@ static void root_factor(Handle& h, Root& rt, int spd, Prec P, void* Aw) {
   // (A = P L U, P a product of in-block row swaps).
   const int NB = 64;
   void* Tbuf = sc.alloc((size_t)NB * n * es);
-  std::vector<int> hp(NB);
   for (int k = 0; k < n; k += NB) {
     int nb = std::min(NB, n - k);
     const int rest = n - k - nb;
     std::vector<LuTask> lt{LuTask{at(Aw, k, k), nb, nb, n, piv + k, info, spd ? 1 : 0}};
     run_getrf(P, lt, sc);
     // block-relative pivots -> absolute rows, then swap the other columns
-    H2_CUDA(cudaMemcpyAsync(hp.data(), piv + k, nb * 4, cudaMemcpyDeviceToHost, s));
-    H2_CUDA(cudaStreamSynchronize(s));
-    for (int q = 0; q < nb; ++q) hp[q] += k;
-    H2_CUDA(cudaMemcpyAsync(piv + k, hp.data(), nb * 4, cudaMemcpyHostToDevice, s));
+    launch_add_offset(piv + k, nb, k, s);
     launch_laswp_cols(P, Aw, n, n, piv, k, k + nb, 0, k, s);
     launch_laswp_cols(P, Aw, n, n, piv, k, k + nb, k + nb, n, s);
     if (rest > 0) {
@@ -1343,27 +1380,15 @@ static void root_factor(Handle& h, Root& rt, int spd, Prec P, void* Aw) {
       gb.run(P, false, false, sc);
     }
   }
-  int hinfo = 0;
-  H2_CUDA(cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, s));
-  H2_CUDA(cudaStreamSynchronize(s));
-  if (hinfo != 0)
-    throw StatusError(spd ? H2_ERR_NOT_SPD : H2_ERR_SINGULAR,
-                      spd ? "non-positive pivot in the top-level Cholesky" : "zero pivot in the top-level LU");
   double* LU = rt.LU->as<double>();
   if (P != Prec::F64) {
     std::vector<CopyTask> ct{CopyTask{Aw, LU, n, n, n, n}};
     run_copy(P, Prec::F64, false, ct, n, n, sc);
   }
-  // log-determinant
+  // log-determinant (read by the caller with the other deferred results)
   {
     std::vector<LuTask> lt{LuTask{LU, n, n, n, piv, nullptr, 0}};
-    double* o = (double*)sc.alloc(16);
-    launch_logdet_lu(sc.up(lt), 1, o, o + 1, false, s);
-    double ho[2];
-    H2_CUDA(cudaMemcpyAsync(ho, o, 16, cudaMemcpyDeviceToHost, s));
-    H2_CUDA(cudaStreamSynchronize(s));
-    rt.logdet = ho[0];
-    rt.sign = ho[1];
+    launch_logdet_lu(sc.up(lt), 1, dlog, dlog + 1, false, s);
   }
   // inverse: X = U^-1 L^-1 P I, blocked by 256-row panels
   rt.inv = std::make_shared<DBuf>((size_t)n * n * 8);
@@ -1397,7 +1422,6 @@ static void root_factor(Handle& h, Root& rt, int spd, Prec P, void* Aw) {
     std::vector<CopyTask> ct{CopyTask{X, rt.inv->p, n, n, n, n}};
     run_copy(P, Prec::F64, false, ct, n, n, sc);
   }
-  H2_CUDA(cudaStreamSynchronize(s));
 }
 
 // ------------------------------------------------------------- factor ----
@@ -1413,6 +1437,28 @@ static void factor(Handle& h, int precision, int spd) {
   const size_t ws = esz(W);
   Points pts = points(h);
   h.level_ms.clear();
+  // Results read back once, after the whole factorization has been issued:
+  // [0] zero / non-positive pivot in a redundant-block LU (any height),
+  // [1] zero pivot in the top-level LU of a problem, then per problem the
+  // top-level log|det| and sign.  Only the ranks are read per height.
+  Scratch fsc(s);
+  const size_t P = h.probs.size();
+  int* dflags = (int*)fsc.alloc(16, true);
+  double* droot = (double*)fsc.alloc(std::max<size_t>(1, P) * 16, true);
+  // scratch budget of the batched pair products (fill-in Gram, projection)
+  size_t pair_budget = size_t(256) << 20;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+      pair_budget = std::min<size_t>(size_t(4) << 30, std::max<size_t>(pair_budget, fr / 8));
+  }
+  std::vector<cudaEvent_t> hev;   // per-height start/end events (factor_ms per level)
+  struct EvGuard {
+    std::vector<cudaEvent_t>& v;
+    ~EvGuard() {
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+  } evguard{hev};
   // near blocks of the current height, in work precision: A[g][q] for the
   // q-th near box of g
   std::vector<std::vector<PairRef>> Ablk;
@@ -1523,17 +1569,15 @@ static void factor(Handle& h, int precision, int spd) {
   std::vector<size_t> t_off;
   std::vector<int64_t> samp;
   for (int H = 0; H < h.Hmax; ++H) {
-    double t0 = now_ms();
+    {
+      cudaEvent_t e0;
+      H2_CUDA(cudaEventCreate(&e0));
+      hev.push_back(e0);
+      H2_CUDA(cudaEventRecord(e0, s));
+    }
     Height& ht = h.hs[H];
     Scratch sc(s);
     const int nb = ht.nb;
-    // scratch budget of the batched pair products (fill-in Gram, projection)
-    size_t pair_budget = size_t(256) << 20;
-    {
-      size_t fr = 0, tot = 0;
-      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
-        pair_budget = std::min<size_t>(size_t(4) << 30, std::max<size_t>(pair_budget, fr / 8));
-    }
     void* pbuf = nullptr;
     size_t pcap = 0;
     auto pair_buf = [&](size_t need) -> void* {   // one buffer shared by the stream-ordered pair loops
@@ -1570,7 +1614,7 @@ static void factor(Handle& h, int precision, int spd) {
       float* dH1 = (float*)sc.alloc((size_t)nb * MLP_WIDTH * 4);
       float* dH2 = (float*)sc.alloc((size_t)nb * MLP_WIDTH * 4);
       float* dY = (float*)sc.alloc((size_t)nb * 4);
-      H2_CUDA(cudaMemcpyAsync(dX, Fh.data(), Fh.size() * 4, cudaMemcpyHostToDevice, s));
+      H2_CUDA(cudaMemcpyAsync(dX, pinned_stage(Fh.data(), Fh.size() * 4, s), Fh.size() * 4, cudaMemcpyHostToDevice, s));
       mlp_forward(m.prm, m.F, dX, nb, dH1, dH2, dY, nullptr, nullptr, s);
       std::vector<float> yh(nb);
       H2_CUDA(cudaMemcpyAsync(yh.data(), dY, (size_t)nb * 4, cudaMemcpyDeviceToHost, s));
@@ -1954,7 +1998,8 @@ static void factor(Handle& h, int precision, int spd) {
       for (int q = 0; q < hr[g]; ++q) ht.sk[g][q] = ht.cand[g][hpiv[(size_t)g * 256 + q]];
     }
     if (std::count(keep_all.begin(), keep_all.end(), 1))
-      H2_CUDA(cudaMemcpyAsync(piv, hpiv.data(), hpiv.size() * 4, cudaMemcpyHostToDevice, s));
+      H2_CUDA(cudaMemcpyAsync(piv, pinned_stage(hpiv.data(), hpiv.size() * 4, s), hpiv.size() * 4,
+                              cudaMemcpyHostToDevice, s));
     std::vector<int>& r = ht.r;
     std::vector<int> m(nb);
     for (int g = 0; g < nb; ++g) m[g] = n[g] - r[g];
@@ -2219,7 +2264,7 @@ static void factor(Handle& h, int precision, int spd) {
     }
     ensure(ht.pivRR, std::max<size_t>(1, ht.pv_off[nb]) * 4);
     ensure(ht.Lt, std::max<size_t>(1, ht.lt_off[nb]) * 8);
-    int* info = (int*)sc.alloc(4, true);
+    int* info = dflags;   // checked once the factorization has been issued
     {
       double* S = ht.S->as<double>();
       std::vector<LuTask> lu;
@@ -2313,12 +2358,6 @@ static void factor(Handle& h, int precision, int spd) {
       }
       run_copy(Prec::F64, W, false, cs, 256, 256, sc);
     }
-    int hinfo = 0;
-    H2_CUDA(cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, s));
-    H2_CUDA(cudaStreamSynchronize(s));
-    if (hinfo != 0)
-      throw StatusError(spd ? H2_ERR_NOT_SPD : H2_ERR_SINGULAR,
-                        spd ? "non-positive pivot in a redundant-block Cholesky" : "zero pivot in a redundant-block LU");
     // ---------------- 5. next height: T = blockdiag(W_a, W_b) ---------
     prof_tag("merge");
     if (up) {
@@ -2335,7 +2374,6 @@ static void factor(Handle& h, int precision, int spd) {
                               r[g], r[g], r[g], up->n[pg]});
       }
       run_copy(Prec::F64, Prec::F64, false, ct, 256, 256, sc);
-      H2_CUDA(cudaStreamSynchronize(s));
       scratch_cache().give(std::move(Tcur), s);
       Tcur = Tn;
       t_off = to;
@@ -2351,28 +2389,53 @@ static void factor(Handle& h, int precision, int spd) {
     ht.y_off.assign(nb + 1, 0);
     for (int g = 0; g < nb; ++g) ht.y_off[g + 1] = ht.y_off[g] + m[g];
     ht.y_len = ht.y_off[nb];
-    H2_CUDA(cudaStreamSynchronize(s));
-    h.level_ms.push_back(now_ms() - t0);
+    {
+      cudaEvent_t e1;
+      H2_CUDA(cudaEventCreate(&e1));
+      hev.push_back(e1);
+      H2_CUDA(cudaEventRecord(e1, s));
+    }
   }
   // roots
   prof_tag("root");
-  for (auto& pb : h.probs) {
-    Root& rt = pb.root;
+  for (size_t p = 0; p < P; ++p) {
+    Root& rt = h.probs[p].root;
     if (rt.n == 0) continue;
     if (W == Prec::F64) {
       Scratch sc(s);
       std::vector<CopyTask> ct{CopyTask{rt.A->p, rt.LU->p, rt.n, rt.n, rt.n, rt.n}};
       run_copy(W, Prec::F64, false, ct, rt.n, rt.n, sc);
-      root_factor(h, rt, spd, Prec::F64, rt.LU->p);
+      root_factor(h, rt, spd, Prec::F64, rt.LU->p, dflags + 1, droot + 2 * p);
     } else {
-      root_factor(h, rt, spd, W, rt.A->p);
+      root_factor(h, rt, spd, W, rt.A->p, dflags + 1, droot + 2 * p);
     }
-    rt.A.reset();
   }
   prof_tag(nullptr);
+  // the deferred results (one synchronisation for the whole factorization)
+  int hflags[4] = {0, 0, 0, 0};
+  std::vector<double> hroot(2 * std::max<size_t>(1, P));
+  H2_CUDA(cudaMemcpyAsync(hflags, dflags, 16, cudaMemcpyDeviceToHost, s));
+  H2_CUDA(cudaMemcpyAsync(hroot.data(), droot, hroot.size() * 8, cudaMemcpyDeviceToHost, s));
   H2_CUDA(cudaStreamSynchronize(s));
+  for (size_t p = 0; p < P; ++p) {
+    Root& rt = h.probs[p].root;
+    rt.A.reset();
+    rt.logdet = rt.n ? hroot[2 * p] : 0.0;
+    rt.sign = rt.n ? hroot[2 * p + 1] : 1.0;
+  }
+  for (size_t k = 0; k + 1 < hev.size(); k += 2) {
+    float ms = 0.f;
+    H2_CUDA(cudaEventElapsedTime(&ms, hev[k], hev[k + 1]));
+    h.level_ms.push_back(ms);
+  }
   if (W == Prec::F32 && tc_error_flag_read_and_clear(s))
     throw StatusError(H2_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+  if (hflags[0])
+    throw StatusError(spd ? H2_ERR_NOT_SPD : H2_ERR_SINGULAR,
+                      spd ? "non-positive pivot in a redundant-block Cholesky" : "zero pivot in a redundant-block LU");
+  if (hflags[1])
+    throw StatusError(spd ? H2_ERR_NOT_SPD : H2_ERR_SINGULAR,
+                      spd ? "non-positive pivot in the top-level Cholesky" : "zero pivot in the top-level LU");
 }
 
 // -------------------------------------------------------------- solve ----
@@ -2596,7 +2659,6 @@ static void construct_impl(h2_handle_* H, int P, const double* const* points, co
   check_opts(kern, opt);
   Handle& h = H->h;
   h.s = (cudaStream_t)stream;
-  H2_CUDA(cudaGetDevice(&h.dev));
   h.kp = KParams{kern->kind, kern->delta, kern->kappa, kern->ell, kern->nugget};
   h.opt = *opt;
   double t0 = now_ms();
@@ -2634,6 +2696,7 @@ static void construct_impl(h2_handle_* H, int P, const double* const* points, co
       perm[pb.off + q] = pb.off + pb.t.perm[q];
     }
   }
+  H2_CUDA(cudaGetDevice(&h.dev));
   h.px.alloc(h.Ntot * 8);
   h.py.alloc(h.Ntot * 8);
   h.pz.alloc(h.Ntot * 8);

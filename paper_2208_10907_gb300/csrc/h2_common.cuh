@@ -250,6 +250,8 @@ void launch_normalize(double* v, const double* w, int64_t n, const double* norm2
 void launch_gather_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int* idx, int64_t n, int nrhs,
                         cudaStream_t s);
 void launch_fill_eye(Prec p, void* A, int n, int ld, cudaStream_t s);
+// p[0:n] += k (block-relative pivots of a panel LU to absolute rows)
+void launch_add_offset(int* p, int n, int k, cudaStream_t s);
 void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int k0, int k1,
                        int col_begin, int col_end, cudaStream_t s);
 void launch_symv_pairs(const SymPairTask* d, int ntasks, const double* x, int64_t ldx, double* part, int nrhs,

@@ -1231,6 +1231,18 @@ void launch_fill_eye(Prec p, void* A, int n, int ld, cudaStream_t s) {
   H2_LAUNCH_CHECK();
 }
 
+__global__ void add_offset_kernel(int* p, int n, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] += k;
+}
+
+void launch_add_offset(int* p, int n, int k, cudaStream_t s) {
+  if (n <= 0) return;
+  ProfScope ps("piv_offset", s);
+  add_offset_kernel<<<(n + NT - 1) / NT, NT, 0, s>>>(p, n, k);
+  H2_LAUNCH_CHECK();
+}
+
 void launch_laswp_cols(Prec p, void* A, int lda, int ncols, const int* piv, int k0, int k1, int cb, int ce,
                        cudaStream_t s) {
   (void)ncols;

@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
     load_chunk(cur_t, 0);
   }
   uint32_t phase[NSTAGE] = {};
+  int committed = 0;                                   // chunks whose MMAs were committed (thread 0)
   for (int c = 0; c < nchunks; ++c) {
     const int st = c % NSTAGE;
     unsigned char* sA_hi = base + st * STAGE_BYTES;
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
             mma_tf32(tmem, smem_desc(aL + off), smem_desc(bH + off), idesc, 1u);
           }
           mma_commit(&mbar[st]);
+          committed = c + 1;
         }
         contigA = (g.flags & 1) != 0;
         contigB = (g.flags & 2) == 0;
@@ -296,16 +298,24 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
             mma_tf32(tmem, smem_desc(aL + off), smem_desc(bH + off), idesc, 1u);
           }
           mma_commit(&mbar[st]);
+          committed = c + 1;
         }
       }
     }
   }
-  // wait for the last commit (it completes after every earlier MMA)
-  if (nchunks > 0) {
-    const int st = (nchunks - 1) % NSTAGE;
-    if (tid == 0 && !s_fail && !mbar_wait(&mbar[st], phase[st])) {
+  // wait for the last commit (it completes after every earlier MMA).  After
+  // a wait that gave up, thread 0 stopped issuing; it still waits (bounded)
+  // for the MMAs it did commit before the TMEM below is released.
+  if (tid == 0 && committed > 0) {
+    const int last = committed - 1;
+    const int st = last % NSTAGE;
+    // phase of the last commit: the waits of chunks last + NSTAGE, ... (if
+    // any happened) toggled phase[st] past it
+    const uint32_t ph = (uint32_t)((last / NSTAGE) & 1);
+    const bool seen = (nchunks - 1 > last);   // a later iteration already waited on it (or gave up)
+    if ((!seen || s_fail) && !mbar_wait(&mbar[st], ph)) {
+      if (!s_fail) atomicExch(err, 1);
       s_fail = 1;
-      atomicExch(err, 1);
     }
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
