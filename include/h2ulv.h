@@ -76,7 +76,7 @@ typedef struct {
   double eta;          /* strong admissibility: far iff max(diam) <= eta*dist */
   int32_t leaf;        /* maximum points per leaf box (<= 256) */
   double tol;          /* relative rank tolerance of the pivoted QR / ID */
-  int32_t max_rank;    /* rank cap (<= 128) */
+  int32_t max_rank;    /* rank cap (<= 256; a parent box then has up to 512 skeletons) */
   int32_t far_s0;      /* far-field sample per far box at the box's level */
   int32_t far_smin;    /* minimum sample per far box */
   int64_t hbm_budget_bytes; /* 0 = no budget check */
@@ -97,7 +97,7 @@ typedef struct h2_handle_* h2_handle;
  *   points : N x 3 row-major doubles (host or device), caller order
  *   N      : number of points, >= 1
  *   kern   : kernel description (host pointer)
- *   opt    : options (host pointer); leaf in [1,256], max_rank in [1,128],
+ *   opt    : options (host pointer); leaf in [1,256], max_rank in [1,256],
  *            tol >= 0, eta > 0
  *   stream : cudaStream_t to issue work on (NULL = default stream)
  *   out    : receives the handle

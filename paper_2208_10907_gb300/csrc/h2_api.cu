@@ -275,7 +275,7 @@ static void validate(const std::vector<GemmTask>& tasks, const std::vector<GemmT
 static void validate(const std::vector<TrsmTask>& v, size_t es) {
   if (!g_check) return;
   for (const TrsmTask& t : v) {
-    if (t.n > 256) throw StatusError(H2_ERR_ARG, "validator: trsm n > 256");
+    if (t.n > NMAX) throw StatusError(H2_ERR_ARG, "validator: trsm n > NMAX");
     check_range(t.A, ext(t.n, t.n, t.lda) * es, "trsm A");
     check_range(t.B, ext(t.n, t.nrhs, t.ldb) * es, "trsm B");
     if (t.piv) check_range(t.piv, (size_t)t.n * 4, "trsm piv");
@@ -298,7 +298,7 @@ static void validate(const std::vector<CopyTask>& v, size_t es_s, size_t es_d, b
 static void validate(const std::vector<CholTask>& v) {
   if (!g_check) return;
   for (const CholTask& t : v) {
-    if (t.n > 256) throw StatusError(H2_ERR_ARG, "validator: pchol n > 256");
+    if (t.n > NMAX) throw StatusError(H2_ERR_ARG, "validator: pchol n > NMAX");
     check_range(t.G, ext(t.n, t.n, t.ldg) * 8, "pchol G");
     check_range(t.R, (size_t)t.n * t.n * 8, "pchol R");
     check_range(t.piv, (size_t)t.n * 4, "pchol piv");
@@ -470,7 +470,9 @@ static void run_trsm(Prec p, bool lower, bool unit, bool tr, const std::vector<T
   validate(v, esz(p));
   double by = 0.0, f = work_trsm(v, esz(p), by);
   prof_note(f, by);
-  launch_trsm(p, lower, unit, tr, sc.up(v), (int)v.size(), maxrhs, sc.s);
+  int maxn = 0;
+  for (const TrsmTask& t : v) maxn = std::max(maxn, t.n);
+  launch_trsm(p, lower, unit, tr, sc.up(v), (int)v.size(), maxrhs, maxn, sc.s);
 }
 static void run_getrf(Prec p, const std::vector<LuTask>& v, Scratch& sc) {
   if (v.empty()) return;
@@ -550,7 +552,9 @@ static void run_fold(const std::vector<FoldTask>& v, const std::vector<FoldTerm>
       }
     }
   prof_note(flops, bytes);
-  launch_fold(sc.up(v), (int)v.size(), sc.up(terms), pts, kp, sc.s);
+  int maxn = 0;
+  for (const FoldTask& t : v) maxn = std::max(maxn, t.n);
+  launch_fold(sc.up(v), (int)v.size(), maxn, sc.up(terms), pts, kp, sc.s);
 }
 // Column-pivoted QR of an n x n triangle stopped at rank r: 4 n^2 r -
 // 2 (n + n) r^2 + 4 r^3 / 3 flops, added once the ranks are read back.
@@ -631,6 +635,7 @@ struct Plan {
     validate(v, esz(p));
     Op o{};
     o.flops = work_trsm(v, esz(p), o.bytes);
+    for (const TrsmTask& t : v) o.b = std::max(o.b, t.n);
     o.kind = 1;
     o.p = p;
     o.f1 = lower;
@@ -712,7 +717,7 @@ struct Plan {
       if (o.flops > 0.0 || o.bytes > 0.0) prof_note(o.flops, o.bytes);
       if (o.kind == 0)
         launch_gemm(o.p, (const GemmTask*)o.tasks, (const GemmTerm*)o.terms, o.n, o.a, o.b, st, false, (int)o.ld);
-      else if (o.kind == 1) launch_trsm(o.p, o.f1, o.f2, o.f3, (const TrsmTask*)o.tasks, o.n, o.a, st);
+      else if (o.kind == 1) launch_trsm(o.p, o.f1, o.f2, o.f3, (const TrsmTask*)o.tasks, o.n, o.a, o.b, st);
       else if (o.kind == 2) launch_copy(o.p, o.p2, o.f1, (const CopyTask*)o.tasks, o.n, o.a, o.b, st);
       else if (o.kind == 3) launch_symv_pairs((const SymPairTask*)o.tasks, o.n, o.x, o.ld, o.y, o.a, st);
       else if (o.kind == 4)
@@ -1090,7 +1095,11 @@ static void build_operator(Handle& h) {
       qt.push_back(PqrTask{R0 + r_off[g], n, n, n, piv + cand_off[g], Rq + r_off[g], rank + g, h.opt.tol,
                            h.opt.max_rank});
     }
-    launch_fold(sc.up(ft), (int)ft.size(), nullptr, pts, h.kp, s);
+    {
+      int maxn = 0;
+      for (const FoldTask& t : ft) maxn = std::max(maxn, t.n);
+      launch_fold(sc.up(ft), (int)ft.size(), maxn, nullptr, pts, h.kp, s);
+    }
     launch_pqr(sc.up(qt), (int)qt.size(), s);
     std::vector<int> hr(ht.nb), hpiv(cand_off[ht.nb]);
     H2_CUDA(cudaMemcpyAsync(hr.data(), rank, ht.nb * 4, cudaMemcpyDeviceToHost, s));
@@ -1667,7 +1676,7 @@ static void factor(Handle& h, int precision, int spd) {
     for (int g = 0; g <= nb; ++g) so[g] = (size_t)g * SL;
     int* finfo = (int*)sc.alloc(4, true);
     void* LUK = sc.alloc(so[nb] * ws);
-    int* pivK = (int*)sc.alloc((size_t)nb * 256 * 4);
+    int* pivK = (int*)sc.alloc((size_t)nb * NMAX * 4);
     void* Mk = sc.alloc(so[nb] * ws, true);
     void* Tmp = sc.alloc(so[nb] * ws);
     {
@@ -1681,7 +1690,7 @@ static void factor(Handle& h, int precision, int spd) {
         int dq = diag_q(g);
         void* dst = (char*)LUK + so[g] * ws;
         ct.push_back(CopyTask{Ablk[g][dq].ptr, dst, n[g], n[g], Ablk[g][dq].ld, n[g]});
-        lu.push_back(LuTask{dst, n[g], n[g], n[g], pivK + (size_t)g * 256, finfo, 0});
+        lu.push_back(LuTask{dst, n[g], n[g], n[g], pivK + (size_t)g * NMAX, finfo, 0});
         if (qr_route) {
           // R_K: rows of [A_KJ]_J^T = columns of every A_KJ, J != K
           FoldTask f{};
@@ -1715,8 +1724,8 @@ static void factor(Handle& h, int precision, int spd) {
       // mixed precision: M_K = A_KK^-1 NG_K A_KK^-T through the explicit
       // inverse A_KK^-1 = U^-1 L^-1 P (two triangular solves on the
       // identity) and two tensor-core GEMMs
-      void* I256 = sc.alloc(256 * 256 * ws);
-      launch_fill_eye(W, I256, 256, 256, s);
+      void* I256 = sc.alloc((size_t)NMAX * NMAX * ws);
+      launch_fill_eye(W, I256, NMAX, NMAX, s);
       std::vector<CopyTask> ci;
       std::vector<TrsmTask> tl, tu;
       GemmBatch x1, x2;
@@ -1725,8 +1734,8 @@ static void factor(Handle& h, int precision, int spd) {
         void* L = (char*)LUK + so[g] * ws;
         void* Ai = (char*)Tmp + so[g] * ws;
         void* M = (char*)Mk + so[g] * ws;
-        ci.push_back(CopyTask{I256, Ai, n[g], n[g], 256, n[g]});
-        tl.push_back(TrsmTask{L, Ai, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
+        ci.push_back(CopyTask{I256, Ai, n[g], n[g], NMAX, n[g]});
+        tl.push_back(TrsmTask{L, Ai, n[g], n[g], n[g], n[g], pivK + (size_t)g * NMAX});
         tu.push_back(TrsmTask{L, Ai, n[g], n[g], n[g], n[g], nullptr});
         x1.add1(L, n[g], n[g], n[g], Ai, n[g], M, n[g], n[g]);      // X = A^-1 NG (over the LU)
         x2.add1(M, n[g], n[g], n[g], L, n[g], Ai, n[g], n[g]);      // M = X A^-T
@@ -1744,7 +1753,7 @@ static void factor(Handle& h, int precision, int spd) {
         if (!has_lu[g]) continue;
         void* L = (char*)LUK + so[g] * ws;
         void* M = (char*)Mk + so[g] * ws;
-        tl.push_back(TrsmTask{L, M, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
+        tl.push_back(TrsmTask{L, M, n[g], n[g], n[g], n[g], pivK + (size_t)g * NMAX});
         tu.push_back(TrsmTask{L, M, n[g], n[g], n[g], n[g], nullptr});
         tr.push_back(CopyTask{M, (char*)Tmp + so[g] * ws, n[g], n[g], n[g], n[g]});
       }
@@ -1756,7 +1765,7 @@ static void factor(Handle& h, int precision, int spd) {
         if (!has_lu[g]) continue;
         void* L = (char*)LUK + so[g] * ws;
         void* X = (char*)Tmp + so[g] * ws;
-        tl2.push_back(TrsmTask{L, X, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
+        tl2.push_back(TrsmTask{L, X, n[g], n[g], n[g], n[g], pivK + (size_t)g * NMAX});
         tu2.push_back(TrsmTask{L, X, n[g], n[g], n[g], n[g], nullptr});
       }
       run_trsm(W, true, true, false, tl2, maxn, sc);
@@ -1771,7 +1780,7 @@ static void factor(Handle& h, int precision, int spd) {
         void* L = (char*)LUK + so[g] * ws;
         void* Z = (char*)Tmp + so[g] * ws;
         tr.push_back(CopyTask{(char*)Mk + so[g] * ws, Z, n[g], n[g], n[g], n[g]});
-        tl.push_back(TrsmTask{L, Z, n[g], n[g], n[g], n[g], pivK + (size_t)g * 256});
+        tl.push_back(TrsmTask{L, Z, n[g], n[g], n[g], n[g], pivK + (size_t)g * NMAX});
         tu.push_back(TrsmTask{L, Z, n[g], n[g], n[g], n[g], nullptr});
       }
       run_copy(W, W, true, tr, maxn, maxn, sc);
@@ -1860,7 +1869,7 @@ static void factor(Handle& h, int precision, int spd) {
     // ---------------- 2. basis with fill-ins (eq. fillu) ---------------
     prof_tag("basis");
     double* R = (double*)sc.alloc(NN * 8);
-    int* piv = (int*)sc.alloc((size_t)nb * 256 * 4);
+    int* piv = (int*)sc.alloc((size_t)nb * NMAX * 4);
     int* rank = (int*)sc.alloc((size_t)nb * 4);
     int* cinfo = (int*)sc.alloc(8, true);   // [0] basis matrix non-finite, [1] fill-in LU zero pivot
     // far-field samples of every box (candidates in point form)
@@ -1917,7 +1926,7 @@ static void factor(Handle& h, int precision, int spd) {
       run_fold(ft, fterms, pts, h.kp, sc);
       std::vector<PqrTask> qt;
       for (int g = 0; g < nb; ++g)
-        qt.push_back(PqrTask{Rpt + off[g], n[g], n[g], n[g], piv + (size_t)g * 256, R + off[g], rank + g, tol_basis,
+        qt.push_back(PqrTask{Rpt + off[g], n[g], n[g], n[g], piv + (size_t)g * NMAX, R + off[g], rank + g, tol_basis,
                              h.opt.max_rank, cinfo});
       run_pqr(qt, sc);
     } else {
@@ -1960,13 +1969,13 @@ static void factor(Handle& h, int precision, int spd) {
       std::vector<CholTask> ct;
       double* Lch = (double*)sc.alloc(NN * 8);
       for (int g = 0; g < nb; ++g)
-        ct.push_back(CholTask{G + off[g], n[g], n[g], piv + (size_t)g * 256, R + off[g], rank + g, tol_basis,
+        ct.push_back(CholTask{G + off[g], n[g], n[g], piv + (size_t)g * NMAX, R + off[g], rank + g, tol_basis,
                               h.opt.max_rank, cinfo, Lch + off[g]});
       run_pchol(ct, sc);
     }
     }
     H2_CUDA(cudaMemcpyAsync(cinfo + 1, finfo, 4, cudaMemcpyDeviceToDevice, s));
-    std::vector<int> hr(nb), hpiv((size_t)nb * 256);
+    std::vector<int> hr(nb), hpiv((size_t)nb * NMAX);
     int hci[2] = {0, 0};
     H2_CUDA(cudaMemcpyAsync(hr.data(), rank, nb * 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaMemcpyAsync(hpiv.data(), piv, hpiv.size() * 4, cudaMemcpyDeviceToHost, s));
@@ -1991,11 +2000,11 @@ static void factor(Handle& h, int precision, int spd) {
       if (hr[g] == 0) {   // empty block row: nothing is redundant
         keep_all[g] = 1;
         hr[g] = n[g];
-        for (int q = 0; q < n[g]; ++q) hpiv[(size_t)g * 256 + q] = q;
+        for (int q = 0; q < n[g]; ++q) hpiv[(size_t)g * NMAX + q] = q;
       }
       ht.r[g] = hr[g];
       ht.sk[g].resize(hr[g]);
-      for (int q = 0; q < hr[g]; ++q) ht.sk[g][q] = ht.cand[g][hpiv[(size_t)g * 256 + q]];
+      for (int q = 0; q < hr[g]; ++q) ht.sk[g][q] = ht.cand[g][hpiv[(size_t)g * NMAX + q]];
     }
     if (std::count(keep_all.begin(), keep_all.end(), 1))
       H2_CUDA(cudaMemcpyAsync(piv, pinned_stage(hpiv.data(), hpiv.size() * 4, s), hpiv.size() * 4,
@@ -2016,7 +2025,7 @@ static void factor(Handle& h, int precision, int spd) {
           tt.push_back(TrsmTask{R + off[g], R + off[g] + (size_t)r[g] * n[g], r[g], n[g] - r[g], n[g], n[g], nullptr});
           maxrhs = std::max(maxrhs, n[g] - r[g]);
         }
-        it.push_back(InterpTask{piv + (size_t)g * 256, R + off[g] + (size_t)r[g] * n[g], P + off[g], n[g], r[g], n[g]});
+        it.push_back(InterpTask{piv + (size_t)g * NMAX, R + off[g] + (size_t)r[g] * n[g], P + off[g], n[g], r[g], n[g]});
       }
       run_trsm(Prec::F64, false, false, false, tt, maxrhs, sc);
       run_interp(Prec::F64, it, sc);
@@ -2305,13 +2314,13 @@ static void factor(Handle& h, int precision, int spd) {
       ensure(ht.Linv, std::max<size_t>(1, ht.li_off[nb]) * 8);
       ensure(ht.Uinv, std::max<size_t>(1, ht.li_off[nb]) * 8);
       {
-        double* I256 = (double*)sc.alloc(256 * 256 * 8);
-        launch_fill_eye(Prec::F64, I256, 256, 256, s);
+        double* I256 = (double*)sc.alloc((size_t)NMAX * NMAX * 8);
+        launch_fill_eye(Prec::F64, I256, NMAX, NMAX, s);
         std::vector<CopyTask> ci;
         for (int g = 0; g < nb; ++g) {
           if (m[g] == 0) continue;
-          ci.push_back(CopyTask{I256, ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], 256, m[g]});
-          ci.push_back(CopyTask{I256, ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], 256, m[g]});
+          ci.push_back(CopyTask{I256, ht.Linv->as<double>() + ht.li_off[g], m[g], m[g], NMAX, m[g]});
+          ci.push_back(CopyTask{I256, ht.Uinv->as<double>() + ht.li_off[g], m[g], m[g], NMAX, m[g]});
         }
         run_copy(Prec::F64, Prec::F64, false, ci, 256, 256, sc);
         if (W == Prec::F64) {
@@ -2649,7 +2658,7 @@ static void check_opts(const h2_kernel* k, const h2_options* o) {
   if (k->kind < 0 || k->kind > 2) throw StatusError(H2_ERR_ARG, "unknown kernel kind");
   if (!(o->eta > 0)) throw StatusError(H2_ERR_ARG, "eta must be > 0");
   if (o->leaf < 1 || o->leaf > 256) throw StatusError(H2_ERR_ARG, "leaf must be in [1, 256]");
-  if (o->max_rank < 1 || o->max_rank > 128) throw StatusError(H2_ERR_ARG, "max_rank must be in [1, 128]");
+  if (o->max_rank < 1 || o->max_rank > 256) throw StatusError(H2_ERR_ARG, "max_rank must be in [1, 256]");
   if (!(o->tol >= 0) || !std::isfinite(o->tol)) throw StatusError(H2_ERR_ARG, "tol must be finite and >= 0");
   if (o->far_s0 < 0 || o->far_smin < 0) throw StatusError(H2_ERR_ARG, "far sample sizes must be >= 0");
 }

@@ -85,6 +85,10 @@ template <> struct KEval<float> {
   }
 };
 
+// Largest box size in level coordinates: a leaf holds at most 256 points and
+// a parent box the skeletons of its two children, r_a + r_b <= 2 * 256.
+constexpr int NMAX = 512;
+
 // Tree-order points, structure of arrays.
 struct Points {
   const double* x;
@@ -226,11 +230,12 @@ void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
 std::string autotune_report();
 void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s);
 void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks,
-                 int maxnrhs, cudaStream_t s);
+                 int maxnrhs, int maxn, cudaStream_t s);
 void launch_pchol(const CholTask* d, int ntasks, cudaStream_t s);
 void launch_pqr(const PqrTask* d, int ntasks, cudaStream_t s);
 void launch_hqr(Prec p, const HqrTask* d, int ntasks, cudaStream_t s);
-void launch_fold(const FoldTask* d, int ntasks, const FoldTerm* terms, Points pts, KParams kp, cudaStream_t s);
+void launch_fold(const FoldTask* d, int ntasks, int maxn, const FoldTerm* terms, Points pts, KParams kp,
+                 cudaStream_t s);
 void launch_kgram(Prec p, const KgramTask* d, int ntasks, int maxn, Points pts, KParams kp,
                   cudaStream_t s);
 void launch_assemble(Prec p, const AsmTask* d, int ntasks, int maxr, int maxc, Points pts,

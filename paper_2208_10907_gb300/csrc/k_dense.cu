@@ -1,4 +1,4 @@
-// Batched small dense linear algebra, one CTA per box (n <= 256).
+// Batched small dense linear algebra, one CTA per box (n <= NMAX = 512).
 //
 // LU with partial pivoting (eq. lu), triangular solves (the eliminations of
 // S^RS and S^SR and the solve sweeps), pivoted Cholesky of a Gram matrix
@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
   // column and the k columns already computed (kept column-major in L so
   // that their reads coalesce), and downdates the diagonal.  Stopping at
   // rank r costs about n r^2 / 2 multiply-adds instead of the n^2 r of
-  // updating the whole trailing matrix.  Thread i owns position i (n <= 256).
+  // updating the whole trailing matrix.  Positions are spread over the
+  // threads (n <= NMAX).
   const CholTask tk = tasks[blockIdx.x];
   const double* G = tk.G;
   const int n = tk.n, ld = tk.ldg;
@@ -256,11 +257,11 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
   double* L = tk.L;    // ld n: L(i, c) at L[i + c n], i in pivoted position order
   __shared__ double s_val[32];
   __shared__ int s_idx[32];
-  __shared__ double d[256];     // diagonal of the remaining Schur complement
-  __shared__ int perm[256];
-  __shared__ double lk[256];    // row k of L
-  const int i = threadIdx.x;
-  if (i < n) {
+  __shared__ double d[NMAX];     // diagonal of the remaining Schur complement
+  __shared__ int perm[NMAX];
+  __shared__ double lk[NMAX];    // row k of L
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += NT) {
     d[i] = G[i + (long long)i * ld];
     perm[i] = i;
   }
@@ -270,15 +271,16 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
   for (int k = 0; k < n; ++k) {
     double best = -INFINITY;
     int bi = 0x7fffffff;
-    if (i >= k && i < n) {
-      best = d[i];
-      bi = i;
-    }
+    for (int i = k + tid; i < n; i += NT)
+      if (d[i] > best || bi == 0x7fffffff) {   // first candidate, then strictly larger (lowest index on ties)
+        best = d[i];
+        bi = i;
+      }
     double pv;
     int p;
     block_argmax(best, bi, s_val, s_idx, pv, p);
     if (p < k || p >= n || pv != pv || pv == INFINITY) {   // non-finite diagonal: stop, flag it
-      if (i == 0 && tk.info) *tk.info = 1;
+      if (tid == 0 && tk.info) *tk.info = 1;
       rank = k;
       break;
     }
@@ -288,12 +290,12 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
       break;
     }
     if (p != k) {
-      if (i < k) {   // rows k and p of the computed columns
-        const double a = L[k + (long long)i * n];
-        L[k + (long long)i * n] = L[p + (long long)i * n];
-        L[p + (long long)i * n] = a;
+      for (int c = tid; c < k; c += NT) {   // rows k and p of the computed columns
+        const double a = L[k + (long long)c * n];
+        L[k + (long long)c * n] = L[p + (long long)c * n];
+        L[p + (long long)c * n] = a;
       }
-      if (i == 0) {
+      if (tid == 0) {
         const double t = d[k];
         d[k] = d[p];
         d[p] = t;
@@ -303,11 +305,11 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
       }
       __syncthreads();
     }
-    if (i < k) lk[i] = L[k + (long long)i * n];
+    for (int c = tid; c < k; c += NT) lk[c] = L[k + (long long)c * n];
     __syncthreads();
     const double rkk = sqrt(d[k]);
-    if (i > k && i < n) {
-      const int pk = perm[k];
+    const int pk = perm[k];
+    for (int i = k + 1 + tid; i < n; i += NT) {
       double c = G[perm[i] + (long long)pk * ld];
       int q = 0;
       double c1 = 0.0, c2 = 0.0, c3 = 0.0;
@@ -324,9 +326,8 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
       const double v = c / rkk;
       L[i + (long long)k * n] = v;
       d[i] -= v * v;
-    } else if (i == k) {
-      L[k + (long long)k * n] = rkk;
     }
+    if (tid == 0) L[k + (long long)k * n] = rkk;
     __syncthreads();
   }
   // R = L^T (rows 0 .. rank-1), zero elsewhere; pivots in position order
@@ -334,12 +335,12 @@ __global__ void __launch_bounds__(NT) pchol_kernel(const CholTask* __restrict__ 
     const int c = e % n, j = e / n;   // R(c, j)
     R[e] = (c < rank && c <= j) ? L[j + (long long)c * n] : 0.0;
   }
-  if (i < n) tk.piv[i] = perm[i];
+  for (int i = tid; i < n; i += NT) tk.piv[i] = perm[i];
   if (threadIdx.x == 0) *tk.rank = rank;
 }
 
 // ---------------------------------------------------------------------------
-// Householder QR with column pivoting (FP64) of an m x n matrix (n <= 256):
+// Householder QR with column pivoting (FP64) of an m x n matrix (n <= NMAX):
 // pivot = remaining column of largest 2-norm, recomputed at every step
 // (ties -> lowest index); stop at |R_kk| <= tol |R_11| or max_rank.
 // ---------------------------------------------------------------------------
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(NT) pqr_kernel(const PqrTask* __restrict__ tas
   double* R = tk.R;
   __shared__ double s_val[32];
   __shared__ int s_idx[32];
-  __shared__ double nrm[256];
+  __shared__ double nrm[NMAX];
   __shared__ double s_beta, s_r11;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = NT / 32;
   for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
@@ -561,17 +562,17 @@ __global__ void __launch_bounds__(NT) hqr_kernel(const HqrTask* __restrict__ tas
 // ---------------------------------------------------------------------------
 constexpr int FC = 32;      // rows per chunk (one per lane of a warp)
 constexpr int FNB = 16;     // panel width of the blocked elimination
-constexpr int FLD = 257;    // leading dimension of the shared row tiles
 
-// Shared state of one fold CTA.
+// Shared state of one fold CTA for boxes of at most NW columns.
+template <int NW>
 struct FoldSmem {
-  double C[FC][FLD];        // the chunk of rows being folded (zero-padded to FC rows)
-  double Rp[FNB][FLD];      // R rows [k0, k0 + nb) of the current panel, columns k0 ..
+  double C[FC][NW + 1];     // the chunk of rows being folded (zero-padded to FC rows)
+  double Rp[FNB][NW + 1];   // R rows [k0, k0 + nb) of the current panel, columns k0 ..
   double V[FC][FNB];        // Householder vectors of the panel (C part; the R part is e_k)
   double T[FNB][FNB];       // block reflector: H_0 ... H_{nb-1} = I - Y T Y^T (upper)
   double tau[FNB];
   double scol[FNB];
-  double cx[256], cy[256], cz[256];
+  double cx[NW], cy[NW], cz[NW];
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -587,7 +588,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // are then accumulated into the compact form I - Y T Y^T and applied to the
 // trailing columns together (W = R_p + V^T C, W <- T^T W, R_p -= W,
 // C -= V W), one column per thread with W in registers.
-__device__ void fold_chunk(double* __restrict__ R, int n, FoldSmem& S) {
+template <int NW>
+__device__ void fold_chunk(double* __restrict__ R, int n, FoldSmem<NW>& S) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
   for (int k0 = 0; k0 < n; k0 += FNB) {
     const int nb = min(FNB, n - k0), w0 = n - k0;
@@ -653,10 +655,9 @@ __device__ void fold_chunk(double* __restrict__ R, int n, FoldSmem& S) {
       }
     }
     __syncthreads();
-    // ---- trailing columns j >= k0 + nb: one column per thread
-    {
-      const int jj = nb + tid;
-      if (jj < w0) {
+    // ---- trailing columns j >= k0 + nb: one column per thread at a time
+    for (int jj = nb + tid; jj < w0; jj += NT) {
+      {
         double w[FNB];
 #pragma unroll
         for (int i = 0; i < FNB; ++i) w[i] = (i < nb) ? S.Rp[i][jj] : 0.0;
@@ -699,13 +700,15 @@ __device__ void fold_chunk(double* __restrict__ R, int n, FoldSmem& S) {
   }
 }
 
-__global__ void __launch_bounds__(NT, 2) fold_kernel(const FoldTask* __restrict__ tasks,
-                                                     const FoldTerm* __restrict__ terms, Points pts, KParams kp) {
+template <int NW>
+__global__ void __launch_bounds__(NT, NW <= 256 ? 2 : 1) fold_kernel(const FoldTask* __restrict__ tasks,
+                                                                    const FoldTerm* __restrict__ terms, Points pts,
+                                                                    KParams kp) {
   const FoldTask tk = tasks[blockIdx.x];
   const int n = tk.n;
   double* R = tk.R;
   extern __shared__ __align__(16) unsigned char fold_raw[];
-  FoldSmem& S = *reinterpret_cast<FoldSmem*>(fold_raw);
+  FoldSmem<NW>& S = *reinterpret_cast<FoldSmem<NW>*>(fold_raw);
   if (!tk.accumulate)
     for (int e = threadIdx.x; e < n * n; e += NT) R[e] = 0.0;
   if (tk.m > 0)
@@ -1045,7 +1048,7 @@ void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s) {
   ProfScope ps(p == Prec::F64 ? "getrf_f64" : "getrf_f32", s);
   // panel rows up to a few thousand (root panels): smem = (m + nc) * sizeof(T)
   // is sized by the caller's maximum via the attribute below.
-  size_t smem = (size_t)(8192 + 256) * (p == Prec::F64 ? 8 : 4);
+  size_t smem = (size_t)(8192 + NMAX) * (p == Prec::F64 ? 8 : 4);
   if (p == Prec::F64) {
     H2_CUDA(cudaFuncSetAttribute(getrf_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     getrf_kernel<double><<<ntasks, NT, smem, s>>>(d);
@@ -1077,12 +1080,13 @@ static void trsm_dispatch(bool lower, bool unit, bool transA, const TrsmTask* d,
 #undef H2_TRSM_CASE
 }
 
-void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks, int maxnrhs,
+void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks, int maxnrhs, int maxn,
                  cudaStream_t s) {
-  if (ntasks <= 0 || maxnrhs <= 0) return;
+  if (ntasks <= 0 || maxnrhs <= 0 || maxn <= 0) return;
+  if (maxn > NMAX) throw StatusError(1, "trsm: triangle larger than NMAX");
   ProfScope ps(p == Prec::F64 ? "trsm_f64" : "trsm_f32", s);
   dim3 grid(ntasks, (maxnrhs + TS_COLS - 1) / TS_COLS);
-  size_t smem = (size_t)256 * (TS_COLS + 1) * (p == Prec::F64 ? 8 : 4);
+  size_t smem = (size_t)maxn * (TS_COLS + 1) * (p == Prec::F64 ? 8 : 4);
   if (p == Prec::F64) trsm_dispatch<double>(lower, unit, transA, d, grid, smem, s);
   else trsm_dispatch<float>(lower, unit, transA, d, grid, smem, s);
   H2_LAUNCH_CHECK();
@@ -1110,13 +1114,21 @@ void launch_hqr(Prec p, const HqrTask* d, int ntasks, cudaStream_t s) {
   H2_LAUNCH_CHECK();
 }
 
-void launch_fold(const FoldTask* d, int ntasks, const FoldTerm* terms, Points pts, KParams kp, cudaStream_t s) {
+template <int NW>
+static void fold_launch(const FoldTask* d, int ntasks, const FoldTerm* terms, Points pts, KParams kp, cudaStream_t s) {
+  size_t smem = sizeof(FoldSmem<NW>);
+  H2_CUDA(cudaFuncSetAttribute(fold_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  H2_CUDA(cudaFuncSetAttribute(fold_kernel<NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  fold_kernel<NW><<<ntasks, NT, smem, s>>>(d, terms, pts, kp);
+}
+
+void launch_fold(const FoldTask* d, int ntasks, int maxn, const FoldTerm* terms, Points pts, KParams kp,
+                 cudaStream_t s) {
   if (ntasks <= 0) return;
+  if (maxn > NMAX) throw StatusError(1, "fold: box wider than NMAX");
   ProfScope ps("fold_f64", s);
-  size_t smem = sizeof(FoldSmem);
-  H2_CUDA(cudaFuncSetAttribute(fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  H2_CUDA(cudaFuncSetAttribute(fold_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  fold_kernel<<<ntasks, NT, smem, s>>>(d, terms, pts, kp);
+  if (maxn <= 256) fold_launch<256>(d, ntasks, terms, pts, kp, s);
+  else fold_launch<NMAX>(d, ntasks, terms, pts, kp, s);
   H2_LAUNCH_CHECK();
 }
 

@@ -47,7 +47,7 @@ def test_argument_errors_need_no_gpu(libpath):
         H.h2_construct(X, 10, H.make_kernel(), H.make_options(leaf=0))
     assert e.value.status == H.H2_ERR_ARG
     with pytest.raises(H.H2Error) as e:
-        H.h2_construct(X, 10, H.make_kernel(), H.make_options(max_rank=129))
+        H.h2_construct(X, 10, H.make_kernel(), H.make_options(max_rank=257))
     assert e.value.status == H.H2_ERR_ARG
     Xn = np.full((10, 3), np.nan)
     with pytest.raises(H.H2Error) as e:

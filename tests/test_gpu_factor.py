@@ -53,6 +53,8 @@ CASES = {
     "surfaces2k_two_levels": (lambda: synth.surface_union(2048, 4), "laplace", 64, 1e-6, 64),
     # leaf 256: n reaches 256 and every rank reaches the cap of 128
     "sphereball16k_leaf256": (lambda: synth.sphere_ball(16384, 21), "yukawa", 256, 1e-10, 128),
+    # rank cap 256: parent boxes reach n = r_a + r_b > 256 (up to 512)
+    "sphereball16k_rank256": (lambda: synth.sphere_ball(16384, 21), "yukawa", 256, 1e-10, 256),
 }
 
 _cache = {}
@@ -114,6 +116,17 @@ def test_fp64_factorization_matches_oracle(name):
         assert ranks == [r for _, r in fac.rank_log]
         if name == "sphereball16k_leaf256":
             assert max(max(r) for r in ranks) == 128 and pb.L - pb.ltop >= 2
+        if name == "sphereball16k_rank256":
+            # boxes wider than 256 at the second ULV level, and ranks above 128
+            assert max(max(r) for r in ranks) > 128
+            assert max(a + b for a, b in zip(ranks[0][0::2], ranks[0][1::2])) > 256
+            # the H^2 operator (its bases up to 256 wide) against the oracle's
+            op = O.H2Operator(pb)
+            xs = synth.rhs(N, 2, 11)
+            xt = torch.from_numpy(np.ascontiguousarray(xs.T)).cuda()
+            yt = torch.zeros_like(xt)
+            H.h2_matvec(h, xt, yt, 2, N)
+            assert rel(yt.cpu().numpy().T, op.matvec(xs)) < 1e-11
         ld, sg = H.h2_logdet(h)
         lo, so = fac.logdet()
         assert sg[0] == so and abs(ld[0] - lo) <= 1e-9 * abs(lo), (ld[0], lo)
