@@ -1977,9 +1977,11 @@ static void factor(Handle& h, int precision, int spd) {
     H2_CUDA(cudaMemcpyAsync(cinfo + 1, finfo, 4, cudaMemcpyDeviceToDevice, s));
     std::vector<int> hr(nb), hpiv((size_t)nb * NMAX);
     int hci[2] = {0, 0};
+    int hprev = 0;   // a redundant-block pivot of an earlier height failed (deferred flag)
     H2_CUDA(cudaMemcpyAsync(hr.data(), rank, nb * 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaMemcpyAsync(hpiv.data(), piv, hpiv.size() * 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaMemcpyAsync(hci, cinfo, 8, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaMemcpyAsync(&hprev, dflags, 4, cudaMemcpyDeviceToHost, s));
     H2_CUDA(cudaStreamSynchronize(s));
     {
       // rank-dependent work of the pivoted Cholesky / pivoted QR just run
@@ -1991,6 +1993,11 @@ static void factor(Handle& h, int precision, int spd) {
       }
       prof_add(qr_route ? "pqr_f64" : "pchol_f64", f);
     }
+    // the first failure is the one reported: a bad pivot below this height
+    // fills everything above it with non-finite values
+    if (hprev)
+      throw StatusError(spd ? H2_ERR_NOT_SPD : H2_ERR_SINGULAR,
+                        spd ? "non-positive pivot in a redundant-block Cholesky" : "zero pivot in a redundant-block LU");
     if (hci[0]) throw StatusError(H2_ERR_NONFINITE, "non-finite value in a basis block row");
     if (hci[1]) throw StatusError(H2_ERR_SINGULAR, "zero or non-finite pivot in a diagonal-block LU (fill-ins)");
     ht.r.resize(nb);

@@ -184,3 +184,33 @@ def test_mixed_factorization_against_oracle_at_effective_tolerance(name):
         assert st_ == H.H2_OK and ach[0] <= 1e-10 and it <= 5, (st_, ach, it)
     finally:
         H.h2_destroy(h)
+
+
+def test_spd_matern_covariance_at_the_rank_cap():
+    """The covariance workload's kernel and factorization, down-scaled:
+    Matern-3/2 (length 0.1, nugget 1e-4) on 16 384 points in the unit cube,
+    leaf 256, tol 1e-8, Cholesky-ULV (spd = 1), rank cap 256.  At this
+    length scale the tolerance needs more than 256 skeletons per box above
+    the leaves, so the bases are truncated at the cap (parent boxes 512
+    wide); the GPU must still reproduce the oracle's factorization of the
+    same truncated operator: ranks box for box, a positive log-det to 1e-9
+    and the unrefined solve to 1e-8."""
+    X = synth.cube(16384, 5)
+    N = len(X)
+    pb = O.Problem(X, "matern32", 256, 1.0, 1e-8, 256)
+    fac = O.ULVFactor(pb, spd=True)
+    b = synth.rhs(N, 1, 3)[:, 0].copy()
+    pts = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    h = H.h2_construct(pts, N, H.make_kernel("matern32"), H.make_options(leaf=256, tol=1e-8, max_rank=256))
+    try:
+        H.h2_factor(h, H.H2_FP64, 1)
+        ranks, st = gpu_ranks(h)
+        assert st["basis_route"] == "qr"
+        assert ranks == [r for _, r in fac.rank_log]
+        assert max(ranks[-1]) == 256 and max(a + b for a, b in zip(ranks[0][0::2], ranks[0][1::2])) > 256
+        ld, sg = H.h2_logdet(h)
+        lo, so = fac.logdet()
+        assert sg[0] == 1 and so == 1 and abs(ld[0] - lo) <= 1e-9 * abs(lo), (ld[0], lo)
+        assert rel(unrefined(h, b), fac.solve(b)) <= 1e-8
+    finally:
+        H.h2_destroy(h)
