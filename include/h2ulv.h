@@ -156,6 +156,27 @@ h2_status h2_solve(h2_handle h, const double* b, double* x, int32_t nrhs, int64_
                    double target_rel_residual, int32_t max_iter,
                    double* achieved_rel_residual, int32_t* iters);
 
+/* Solve every problem of a batched handle with its own right-hand sides
+ * (Sec. II-B solve and the FP64 refinement of h2_solve), all problems in the
+ * same launches.
+ *   b[p], x[p] : N[p] x nrhs[p] column-major, leading dimension ld[p] >= N[p]
+ *                (host or device), in problem p's caller order
+ *   nrhs[p]    : right-hand sides of problem p (>= 1)
+ *   achieved_rel_residual : host array of P (may be NULL): per problem, the
+ *                largest ||b - A_H2 x|| / ||b|| over its columns
+ *   iters      : host int, corrections applied (may be NULL)
+ * The columns are stacked and padded with zero columns to the largest
+ * nrhs[p], so the cost is that of max_p nrhs[p] columns over all problems.
+ * The refinement is the stationary one (x <- x + ULV^-1 (b - A_H2 x)), which
+ * acts on each problem separately, and every column of every problem must
+ * reach the target on its own norm.  Stacked work buffers are kept by the
+ * handle between calls.
+ * Errors: H2_ERR_STATE (not factored), H2_ERR_ARG, H2_ERR_NONFINITE,
+ * H2_ERR_NOT_CONVERGED (x still holds the last iterate). */
+h2_status h2_solve_batched(h2_handle h, const double* const* b, double* const* x, const int32_t* nrhs,
+                           const int64_t* ld, double target_rel_residual, int32_t max_iter,
+                           double* achieved_rel_residual, int32_t* iters);
+
 /* y = A_H2 x, the H^2 operator used as the refinement residual (near blocks
  * exact, far blocks through the nested bases, eq. transfer).
  *   x, y : N x nrhs column-major, leading dimension ld (host or device)

@@ -863,6 +863,10 @@ struct Handle {
     std::vector<DBufP> bufs;
   };
   std::map<int, std::shared_ptr<SolvePlans>> plans;
+  DBufP bstage, xstage;              // stacked right-hand sides / solutions (h2_solve_batched)
+  bool per_problem = false;          // refinement checks every problem's columns on their own norms
+  DBufP segnrm;                      // per (problem, column) squared norms
+  std::vector<double> last_rel;      // per (problem, column) relative residuals of the last solve
   double t_construct_ms = 0, t_factor_ms = 0;
   std::vector<double> level_ms;
   // rank predictor (optional)
@@ -2998,14 +3002,32 @@ h2_status h2_solve(h2_handle H, const double* b, double* x, int32_t nrhs, int64_
     auto& sp = solve_plans(h, nrhs, true);
     to_tree(h, b, ld, nrhs, sp.B, sp.Uin);
     launch_colnorm2(sp.B, (int)N, nrhs, N, sp.nrm, h.s);
-    std::vector<double> bn(nrhs), rn(nrhs);
+    std::vector<double> bn(nrhs);
     H2_CUDA(cudaMemcpyAsync(bn.data(), sp.nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
     H2_CUDA(cudaStreamSynchronize(h.s));
     for (double v : bn)
       if (!std::isfinite(v)) throw StatusError(H2_ERR_NONFINITE, "non-finite right-hand side");
     std::vector<double> rel(nrhs, 0.0);
     const char* mode = getenv("H2_REFINE");
-    const bool use_gmres = nrhs <= 8 && !(mode && std::string(mode) == "stationary");
+    const bool use_gmres = nrhs <= 8 && !(mode && std::string(mode) == "stationary") && !h.per_problem;
+    // squared column norms per problem segment (tree-order rows [off, off + N))
+    // when every problem is checked on its own, else over the whole column
+    const size_t nseg = h.per_problem ? h.probs.size() : 1;
+    std::vector<double> bseg(nseg * nrhs), rseg(nseg * nrhs);
+    auto seg_norms = [&](const double* V, std::vector<double>& out) {
+      if (nseg == 1) {
+        launch_colnorm2(V, (int)N, nrhs, N, sp.nrm, h.s);
+        H2_CUDA(cudaMemcpyAsync(out.data(), sp.nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
+      } else {
+        ensure(h.segnrm, nseg * nrhs * 8);
+        double* d = h.segnrm->as<double>();
+        for (size_t q = 0; q < nseg; ++q)
+          launch_colnorm2(V + h.probs[q].off, (int)h.probs[q].t.N, nrhs, N, d + q * nrhs, h.s);
+        H2_CUDA(cudaMemcpyAsync(out.data(), d, nseg * nrhs * 8, cudaMemcpyDeviceToHost, h.s));
+      }
+      H2_CUDA(cudaStreamSynchronize(h.s));
+    };
+    if (nseg > 1) seg_norms(sp.B, bseg);
     if (use_gmres) {
       int it = 0;
       bool conv = false;
@@ -3022,18 +3044,22 @@ h2_status h2_solve(h2_handle H, const double* b, double* x, int32_t nrhs, int64_
     sp.ulv->run(h.s);
     H2_CUDA(cudaMemcpyAsync(sp.X, sp.Uout, bytes, cudaMemcpyDeviceToDevice, h.s));
     int it = 0;
+    if (nseg == 1) bseg = bn;
     while (true) {
       sp.mv->run(h.s);                                               // R = A_H2 X
       launch_axpy_cols(sp.R, sp.B, (int)N, nrhs, N, N, -1.0, h.s);   // R = A X - b
-      launch_colnorm2(sp.R, (int)N, nrhs, N, sp.nrm, h.s);
-      H2_CUDA(cudaMemcpyAsync(rn.data(), sp.nrm, nrhs * 8, cudaMemcpyDeviceToHost, h.s));
-      H2_CUDA(cudaStreamSynchronize(h.s));
+      seg_norms(sp.R, rseg);
       bool ok = true;
-      for (int c = 0; c < nrhs; ++c) {
-        double den = bn[c] > 0 ? std::sqrt(bn[c]) : 1.0;
-        rel[c] = std::sqrt(rn[c]) / den;
-        if (!(rel[c] <= target)) ok = false;
-      }
+      std::fill(rel.begin(), rel.end(), 0.0);
+      h.last_rel.assign(nseg * nrhs, 0.0);
+      for (size_t q = 0; q < nseg; ++q)
+        for (int c = 0; c < nrhs; ++c) {
+          const double bq = bseg[q * nrhs + c];
+          const double rq = bq > 0 ? std::sqrt(rseg[q * nrhs + c]) / std::sqrt(bq) : std::sqrt(rseg[q * nrhs + c]);
+          h.last_rel[q * nrhs + c] = rq;
+          rel[c] = std::max(rel[c], rq);
+          if (!(rq <= target)) ok = false;
+        }
       if (ok || it >= max_iter) {
         converged = ok;
         break;
@@ -3054,6 +3080,71 @@ h2_status h2_solve(h2_handle H, const double* b, double* x, int32_t nrhs, int64_
     return H2_ERR_NOT_CONVERGED;
   }
   return st;
+}
+
+h2_status h2_solve_batched(h2_handle H, const double* const* b, double* const* x, const int32_t* nrhs,
+                           const int64_t* ld, double target, int32_t max_iter, double* achieved, int32_t* iters) {
+  if (!H || !b || !x || !nrhs || !ld || max_iter < 0) {
+    g_err = "invalid batched solve arguments";
+    return H2_ERR_ARG;
+  }
+  if (!H->h.factored) {
+    g_err = "h2_solve_batched before h2_factor";
+    return H2_ERR_STATE;
+  }
+  Handle& h = H->h;
+  const size_t P = h.probs.size();
+  int nmax = 0;
+  for (size_t p = 0; p < P; ++p) {
+    const int64_t Np = h.probs[p].t.N;
+    if (!b[p] || !x[p] || nrhs[p] < 1 || ld[p] < Np) {
+      g_err = "invalid batched solve arguments (problem " + std::to_string(p) + ")";
+      return H2_ERR_ARG;
+    }
+    nmax = std::max(nmax, (int)nrhs[p]);
+  }
+  std::vector<double> ach((size_t)nmax, 0.0);
+  int it = 0;
+  h2_status st = guard([&] {
+    // stack the problems' columns (rows by problem, caller order), zero-padded
+    // to the largest count: a zero column is solved exactly at no extra sweep
+    const size_t bytes = (size_t)h.Ntot * nmax * 8;
+    ensure(h.bstage, bytes);
+    ensure(h.xstage, bytes);
+    double* B = h.bstage->as<double>();
+    H2_CUDA(cudaMemsetAsync(B, 0, bytes, h.s));
+    for (size_t p = 0; p < P; ++p) {
+      const int64_t Np = h.probs[p].t.N;
+      H2_CUDA(cudaMemcpy2DAsync(B + h.probs[p].off, (size_t)h.Ntot * 8, b[p], (size_t)ld[p] * 8, (size_t)Np * 8,
+                                nrhs[p], cudaMemcpyDefault, h.s));
+    }
+  });
+  if (st != H2_OK) return st;
+  h.per_problem = true;
+  const h2_status sst = h2_solve(H, h.bstage->as<double>(), h.xstage->as<double>(), nmax, h.Ntot, target, max_iter,
+                                 ach.data(), &it);
+  h.per_problem = false;
+  if (sst != H2_OK && sst != H2_ERR_NOT_CONVERGED) return sst;
+  st = guard([&] {
+    const double* X = h.xstage->as<double>();
+    for (size_t p = 0; p < P; ++p) {
+      const int64_t Np = h.probs[p].t.N;
+      H2_CUDA(cudaMemcpy2DAsync(x[p], (size_t)ld[p] * 8, X + h.probs[p].off, (size_t)h.Ntot * 8, (size_t)Np * 8,
+                                nrhs[p], cudaMemcpyDefault, h.s));
+    }
+    H2_CUDA(cudaStreamSynchronize(h.s));
+  });
+  if (st != H2_OK) return st;
+  if (achieved)   // per problem: the largest relative residual over its own columns
+    for (size_t p = 0; p < P; ++p) {
+      double a = 0.0;
+      for (int c = 0; c < nrhs[p]; ++c)
+        a = std::max(a, h.last_rel.size() == P * (size_t)nmax ? h.last_rel[p * nmax + c] : ach[c]);
+      achieved[p] = a;
+    }
+  if (iters) *iters = it;
+  if (sst == H2_ERR_NOT_CONVERGED) g_err = "refinement did not reach the target residual";
+  return sst;
 }
 
 h2_status h2_logdet(h2_handle H, double* log_abs_det, int32_t* sign) {

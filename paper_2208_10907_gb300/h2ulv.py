@@ -20,7 +20,7 @@ H2_K_LAPLACE, H2_K_YUKAWA, H2_K_MATERN32 = 0, 1, 2
 H2_FP64, H2_MIXED = 0, 1
 KERNEL_KIND = {"laplace": H2_K_LAPLACE, "yukawa": H2_K_YUKAWA, "matern32": H2_K_MATERN32}
 
-EXPORTED = ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_matvec",
+EXPORTED = ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_solve_batched", "h2_matvec",
             "h2_logdet", "h2_logdet_noalloc", "h2_stats", "h2_profile", "h2_last_error", "h2_destroy",
             "h2_mlp_param_count", "h2_mlp_create", "h2_mlp_train", "h2_mlp_forward", "h2_mlp_gradient",
             "h2_mlp_params", "h2_mlp_last_error", "h2_mlp_destroy", "h2_box_features", "h2_set_rank_predictor")
@@ -60,6 +60,8 @@ def lib():
                                            ctypes.POINTER(h2_options), vp, ctypes.POINTER(vp)]
         L.h2_factor.argtypes = [vp, i32, i32]
         L.h2_solve.argtypes = [vp, vp, vp, i32, i64, dp, i32, vp, ctypes.POINTER(i32)]
+        L.h2_solve_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i64), dp, i32, vp, ctypes.POINTER(i32)]
         L.h2_matvec.argtypes = [vp, vp, vp, i32, i64]
         L.h2_logdet.argtypes = [vp, vp, vp]
         L.h2_logdet_noalloc.argtypes = [vp, vp, vp]
@@ -82,7 +84,8 @@ def lib():
             getattr(L, f).restype = ctypes.c_int
         L.h2_last_error.restype = ctypes.c_char_p
         L.h2_destroy.argtypes = [vp]
-        for f in ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_matvec", "h2_logdet",
+        for f in ("h2_construct", "h2_construct_batched", "h2_factor", "h2_solve", "h2_solve_batched", "h2_matvec",
+                  "h2_logdet",
                   "h2_logdet_noalloc", "h2_stats", "h2_profile"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -141,6 +144,23 @@ def h2_solve(h, b, x, nrhs, ld, target=1e-10, max_iter=20, check=True):
     it = ctypes.c_int32(0)
     st = lib().h2_solve(h, _ptr(b), _ptr(x), int(nrhs), int(ld), float(target), int(max_iter),
                         ctypes.c_void_p(ach.ctypes.data), ctypes.byref(it))
+    if check and st not in (H2_OK, H2_ERR_NOT_CONVERGED):
+        _check(st)
+    return st, ach, it.value
+
+
+def h2_solve_batched(h, bs, xs, nrhs, lds, target=1e-10, max_iter=20, check=True):
+    """Per-problem right-hand sides of a batched handle.  Returns (status,
+    per-problem achieved relative residuals, corrections applied)."""
+    P = len(bs)
+    bp = (ctypes.c_void_p * P)(*[_ptr(b).value for b in bs])
+    xp = (ctypes.c_void_p * P)(*[_ptr(x).value for x in xs])
+    nr = (ctypes.c_int32 * P)(*[int(v) for v in nrhs])
+    ld = (ctypes.c_int64 * P)(*[int(v) for v in lds])
+    ach = np.zeros(P, dtype=np.float64)
+    it = ctypes.c_int32(0)
+    st = lib().h2_solve_batched(h, bp, xp, nr, ld, float(target), int(max_iter), ctypes.c_void_p(ach.ctypes.data),
+                                ctypes.byref(it))
     if check and st not in (H2_OK, H2_ERR_NOT_CONVERGED):
         _check(st)
     return st, ach, it.value
