@@ -300,6 +300,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64-path steps (0 = skip)")
     ap.add_argument("--kernel-table", action="store_true", help="print the per-kernel event table to stderr")
+    ap.add_argument("--partition", default="bisection", choices=["bisection", "kmeans"],
+                    help="cluster tree of the headline workload (the default is the workload's bisection)")
     ap.add_argument("--workload", default="surfaces1m", choices=["surfaces1m", "batched64"],
                     help="batched64: the 64 independent problems of the batched workload (not the headline)")
     args = ap.parse_args()
@@ -328,7 +330,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     kern = H.make_kernel(W["kernel"])
     opt = H.make_options(eta=W["eta"], leaf=W["leaf"], tol=W["tol"], max_rank=W["max_rank"], far_s0=W["far_s0"],
-                         far_smin=W["far_smin"], hbm_budget_bytes=180 * 10**9)
+                         far_smin=W["far_smin"], hbm_budget_bytes=180 * 10**9, partition=args.partition)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = H.h2_construct(pts, n, kern, opt, stream.cuda_stream)
@@ -461,6 +463,7 @@ def main():
                                    "leaf 256, eta 1, tol 1e-6, mixed factor refined to H2 residual 1e-10",
                        "n": n, "leaf": W["leaf"], "eta": W["eta"], "tol": W["tol"], "max_rank": W["max_rank"],
                        "far_sample": [W["far_s0"], W["far_smin"]], "l2": "inputs larger than L2 (tens of GB)",
+                       "partition": args.partition,
                        "residual": "FP64 H2 operator; its near field for one right-hand side in double-float "
                                    "(FP64 entries split exactly into FP32 pairs, about 2^-46 per product)",
                        "basis": {"route": st_m.get("basis_route"), "tol_basis": st_m.get("tol_basis")},

@@ -80,6 +80,11 @@ typedef struct {
   int32_t far_s0;      /* far-field sample per far box at the box's level */
   int32_t far_smin;    /* minimum sample per far box */
   int64_t hbm_budget_bytes; /* 0 = no budget check */
+  int32_t partition;   /* cluster tree: 0 = coordinate bisection (split along the
+                          longest side at the median), 1 = balanced 2-means
+                          (Sec. V's k-means partition with a power-of-two number of
+                          leaves: every box split into its floor(n/2) points nearest
+                          one Lloyd centroid and the rest) */
 } h2_options;
 
 /* Precision of the factorization.  The rank decisions (pivoted QR/ID), the

@@ -9,7 +9,7 @@ use is ``synth`` (seeded inputs, no solver arithmetic).
 Every function follows a passage of the paper (Ma, Deshmukh, Yokota,
 "Scalable Linear Time Dense Direct Solver for 3-D Problems Without Trailing
 Sub-Matrix Dependencies", arXiv 2208.10907).  Where the paper is silent the
-reading taken is named (O-1 ... O-12) at the code that applies it.
+reading taken is named (O-1 ... O-15) at the code that applies it.
 
 Notation (Sec. II-A, Fig. "notation"): a box I at level l owns n_I
 "level coordinates"; Q_I = [U^R_I U^S_I] is its orthogonal basis, r_I its
@@ -70,6 +70,69 @@ def cluster_tree(X, leaf):
             ax = int(np.argmax(ext))
             order = np.lexsort((idx, P[:, ax]))
             perm[s:e] = idx[order]
+            mid = s + (e - s) // 2
+            nxt += [(s, mid), (mid, e)]
+        boxes.append(nxt)
+    return L, perm, boxes
+
+
+# ----------------------------------------------------------------------------
+# O-15  k-means partition (Sec. V: a 3-D k-means clustering forms the leaf
+# boxes, with the number of clusters a power of two).  Reading: every box is
+# split by a balanced 2-means (Lloyd iterations whose assignment step gives
+# the floor(n/2) points closest to centroid 0 relative to centroid 1 to the
+# left child), which keeps the full binary tree of 2^L leaves.  Seeds: the
+# point farthest from the box's mean, then the point farthest from that one.
+# Sums run over the box's points in increasing caller index, distances are
+# ((dx^2 + dy^2) + dz^2), ties go to the lowest caller index, at most 20
+# Lloyd steps.
+# ----------------------------------------------------------------------------
+def _seq_mean(P):
+    return np.array([np.cumsum(P[:, a])[-1] for a in range(3)]) / len(P)
+
+
+def _sqdist(P, c):
+    return ((P[:, 0] - c[0]) ** 2 + (P[:, 1] - c[1]) ** 2) + (P[:, 2] - c[2]) ** 2
+
+
+def balanced_two_means(X, idx, iters=20):
+    """Order the caller indices idx of one box as [left child, right child]
+    (left = the first floor(n/2)); returns (order, Lloyd steps taken)."""
+    idx = np.sort(np.asarray(idx))
+    n = len(idx)
+    P = X[idx]
+    if n < 2:
+        return idx, 0
+    a = int(np.argmax(_sqdist(P, _seq_mean(P))))
+    c0 = P[a].copy()
+    b = int(np.argmax(_sqdist(P, c0)))
+    c1 = P[b].copy()
+    left = None
+    h = n // 2
+    for it in range(iters):
+        key = _sqdist(P, c0) - _sqdist(P, c1)
+        order = np.lexsort((idx, key))
+        new_left = np.sort(order[:h])
+        if left is not None and np.array_equal(new_left, left):
+            return idx[order], it
+        left = new_left
+        right = np.sort(order[h:])
+        c0 = _seq_mean(P[left])
+        c1 = _seq_mean(P[right])
+    key = _sqdist(P, c0) - _sqdist(P, c1)
+    return idx[np.lexsort((idx, key))], iters
+
+
+def cluster_tree_kmeans(X, leaf):
+    """Same outputs as cluster_tree, with every split a balanced 2-means."""
+    N = len(X)
+    L = int(np.ceil(np.log2(N / leaf))) if N > leaf else 0
+    perm = np.arange(N)
+    boxes = [[(0, N)]]
+    for _ in range(L):
+        nxt = []
+        for (s, e) in boxes[-1]:
+            perm[s:e] = balanced_two_means(X, perm[s:e])[0]
             mid = s + (e - s) // 2
             nxt += [(s, mid), (mid, e)]
         boxes.append(nxt)
@@ -259,14 +322,17 @@ def interpolation_matrix(piv, R, rank, n):
 # shared basis"), nested through transfer matrices (eq. transfer).
 # ----------------------------------------------------------------------------
 class Problem:
-    def __init__(self, X, kernel, leaf, eta, tol, max_rank, s0=32, s_min=4, kparams=None):
+    def __init__(self, X, kernel, leaf, eta, tol, max_rank, s0=32, s_min=4, kparams=None, partition="bisection"):
         self.X = np.asarray(X, dtype=np.float64)
         self.N = len(self.X)
         self.kernel = kernel
         self.kp = dict(kparams or {})
         self.leaf, self.eta, self.tol, self.max_rank = leaf, eta, tol, max_rank
         self.s0, self.s_min = s0, s_min
-        self.L, self.perm, self.boxes = cluster_tree(self.X, leaf)
+        if partition == "kmeans":
+            self.L, self.perm, self.boxes = cluster_tree_kmeans(self.X, leaf)
+        else:
+            self.L, self.perm, self.boxes = cluster_tree(self.X, leaf)
         self.Xt = self.X[self.perm]
         self.near, self.far = interaction_lists(self.Xt, self.boxes, self.L, eta)
         self.ltop = top_level(self.far, self.L)

@@ -2672,6 +2672,7 @@ static void check_opts(const h2_kernel* k, const h2_options* o) {
   if (o->max_rank < 1 || o->max_rank > 256) throw StatusError(H2_ERR_ARG, "max_rank must be in [1, 256]");
   if (!(o->tol >= 0) || !std::isfinite(o->tol)) throw StatusError(H2_ERR_ARG, "tol must be finite and >= 0");
   if (o->far_s0 < 0 || o->far_smin < 0) throw StatusError(H2_ERR_ARG, "far sample sizes must be >= 0");
+  if (o->partition != 0 && o->partition != 1) throw StatusError(H2_ERR_ARG, "partition must be 0 or 1");
 }
 
 static void construct_impl(h2_handle_* H, int P, const double* const* points, const int64_t* N,
@@ -2698,7 +2699,7 @@ static void construct_impl(h2_handle_* H, int P, const double* const* points, co
     for (double v : host)
       if (!std::isfinite(v)) throw StatusError(H2_ERR_NONFINITE, "non-finite coordinate");
     Problem& pb = h.probs[p];
-    pb.t = build_tree(host.data(), N[p], opt->leaf, opt->eta);
+    pb.t = build_tree(host.data(), N[p], opt->leaf, opt->eta, opt->partition);
     pb.off = off;
     pb.H = pb.t.L - pb.t.ltop;
     off += N[p];

@@ -39,7 +39,78 @@ static bool admissible(const Box& a, const Box& b, double eta) {
   return std::max(da, db) <= eta * dist;
 }
 
-Tree build_tree(const double* P, int64_t N, int leaf, double eta) {
+// Balanced 2-means split of one box (Sec. V's k-means partition, with the
+// number of clusters kept a power of two): order the box's caller indices
+// as [left child, right child], left = the floor(n/2) points with the
+// smallest |x - c0|^2 - |x - c1|^2, then move c0, c1 to the children's
+// means and repeat (at most 20 steps) until the left child stops changing.
+// Seeds: the point farthest from the box's mean and the point farthest from
+// that one.  Sums run in increasing caller index, squared distances are
+// ((dx^2 + dy^2) + dz^2), ties go to the lowest caller index; with the host
+// code compiled without floating-point contraction every host rounds the
+// same way.
+static void balanced_two_means(const double* P, int64_t* first, int64_t* last) {
+  const int64_t n = last - first;
+  if (n < 2) return;
+  std::vector<int64_t> idx(first, last);
+  std::sort(idx.begin(), idx.end());
+  auto mean = [&](const std::vector<int64_t>& v, double c[3]) {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t i : v) {
+      sx += P[3 * i];
+      sy += P[3 * i + 1];
+      sz += P[3 * i + 2];
+    }
+    c[0] = sx / (double)v.size();
+    c[1] = sy / (double)v.size();
+    c[2] = sz / (double)v.size();
+  };
+  auto d2 = [&](int64_t i, const double c[3]) {
+    const double dx = P[3 * i] - c[0], dy = P[3 * i + 1] - c[1], dz = P[3 * i + 2] - c[2];
+    return (dx * dx + dy * dy) + dz * dz;
+  };
+  auto farthest = [&](const double c[3]) {
+    int64_t best = idx[0];
+    double bd = d2(idx[0], c);
+    for (int64_t i : idx) {
+      const double v = d2(i, c);
+      if (v > bd) {
+        bd = v;
+        best = i;
+      }
+    }
+    return best;
+  };
+  double m[3], c0[3], c1[3];
+  mean(idx, m);
+  const int64_t a = farthest(m);
+  for (int k = 0; k < 3; ++k) c0[k] = P[3 * a + k];
+  const int64_t b = farthest(c0);
+  for (int k = 0; k < 3; ++k) c1[k] = P[3 * b + k];
+  const int64_t h = n / 2;
+  std::vector<std::pair<double, int64_t>> key(n);
+  std::vector<int64_t> left, prev, right;
+  auto assign = [&]() {
+    for (int64_t q = 0; q < n; ++q) key[q] = {d2(idx[q], c0) - d2(idx[q], c1), idx[q]};
+    std::sort(key.begin(), key.end());
+  };
+  for (int it = 0; it < 20; ++it) {
+    assign();
+    left.clear();
+    right.clear();
+    for (int64_t q = 0; q < n; ++q) (q < h ? left : right).push_back(key[q].second);
+    std::sort(left.begin(), left.end());
+    std::sort(right.begin(), right.end());
+    if (it > 0 && left == prev) break;
+    prev = left;
+    mean(left, c0);
+    mean(right, c1);
+    if (it == 19) assign();
+  }
+  for (int64_t q = 0; q < n; ++q) first[q] = key[q].second;
+}
+
+Tree build_tree(const double* P, int64_t N, int leaf, double eta, int partition) {
   Tree t;
   t.N = N;
   t.L = N > leaf ? (int)std::ceil(std::log2((double)N / (double)leaf)) : 0;
@@ -50,6 +121,13 @@ Tree build_tree(const double* P, int64_t N, int leaf, double eta) {
   std::vector<int64_t> tmp;
   for (int l = 0; l < t.L; ++l) {
     for (const Box& b : t.boxes[l]) {
+      if (partition == 1) {
+        balanced_two_means(P, t.perm.data() + b.s, t.perm.data() + b.e);
+        int64_t mid = b.s + (b.e - b.s) / 2;
+        t.boxes[l + 1].push_back(Box{b.s, mid, {0, 0, 0}, {0, 0, 0}});
+        t.boxes[l + 1].push_back(Box{mid, b.e, {0, 0, 0}, {0, 0, 0}});
+        continue;
+      }
       // bounding box of the caller points of this box
       double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
       for (int64_t q = b.s; q < b.e; ++q) {

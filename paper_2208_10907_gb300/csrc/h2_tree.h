@@ -20,10 +20,11 @@ struct Tree {
   std::vector<double> xt, yt, zt;                  // tree-order coordinates
 };
 
-// Coordinate-bisection tree (full binary, 2^L leaves, L = ceil(log2(N/leaf)))
-// and the near / far lists of strong admissibility
+// Cluster tree (full binary, 2^L leaves, L = ceil(log2(N/leaf))) by
+// coordinate bisection (partition 0) or balanced 2-means (partition 1), and
+// the near / far lists of strong admissibility
 // max(diam I, diam J) <= eta * dist(I, J).
-Tree build_tree(const double* pts_rowmajor, int64_t N, int leaf, double eta);
+Tree build_tree(const double* pts_rowmajor, int64_t N, int leaf, double eta, int partition);
 
 // Far-field sample of box i at level l (tree-order indices within the
 // problem): the far boxes of level l' (l' = l, l-1, ..., 1, along i's

@@ -34,7 +34,7 @@ class h2_kernel(ctypes.Structure):
 class h2_options(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("leaf", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_rank", ctypes.c_int32), ("far_s0", ctypes.c_int32), ("far_smin", ctypes.c_int32),
-                ("hbm_budget_bytes", ctypes.c_int64)]
+                ("hbm_budget_bytes", ctypes.c_int64), ("partition", ctypes.c_int32)]
 
 
 class H2Error(RuntimeError):
@@ -112,8 +112,12 @@ def make_kernel(kind="laplace", delta=1e-3, kappa=1.0, ell=0.1, nugget=1e-4):
     return h2_kernel(KERNEL_KIND.get(kind, kind), delta, kappa, ell, nugget)
 
 
-def make_options(eta=1.0, leaf=256, tol=1e-8, max_rank=128, far_s0=32, far_smin=4, hbm_budget_bytes=0):
-    return h2_options(eta, leaf, tol, max_rank, far_s0, far_smin, hbm_budget_bytes)
+PARTITION = {"bisection": 0, "kmeans": 1}
+
+
+def make_options(eta=1.0, leaf=256, tol=1e-8, max_rank=128, far_s0=32, far_smin=4, hbm_budget_bytes=0,
+                 partition="bisection"):
+    return h2_options(eta, leaf, tol, max_rank, far_s0, far_smin, hbm_budget_bytes, PARTITION.get(partition, partition))
 
 
 def h2_construct(points, N, kernel, options, stream=None):

@@ -214,3 +214,38 @@ def test_spd_matern_covariance_at_the_rank_cap():
         assert rel(unrefined(h, b), fac.solve(b)) <= 1e-8
     finally:
         H.h2_destroy(h)
+
+
+def test_kmeans_partition_through_the_library():
+    """The k-means partition (Sec. V; balanced 2-means splits, partition =
+    1) through the library on a surface cloud: the H^2 operator, the ranks,
+    the FP64 log-det and the refined solution match the oracle built on the
+    same k-means tree."""
+    X = synth.surface_union(8192, 4)
+    N = len(X)
+    pb = O.Problem(X, "laplace", 128, 1.0, 1e-8, 128, partition="kmeans")
+    fac = O.ULVFactor(pb)
+    op = O.H2Operator(pb)
+    pts = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    h = H.h2_construct(pts, N, H.make_kernel("laplace"),
+                       H.make_options(leaf=128, tol=1e-8, max_rank=128, partition="kmeans"))
+    try:
+        xs = synth.rhs(N, 2, 13)
+        xt = torch.from_numpy(np.ascontiguousarray(xs.T)).cuda()
+        yt = torch.zeros_like(xt)
+        H.h2_matvec(h, xt, yt, 2, N)
+        assert rel(yt.cpu().numpy().T, op.matvec(xs)) < 1e-11
+        H.h2_factor(h, H.H2_FP64)
+        ranks, _ = gpu_ranks(h)
+        assert ranks == [r for _, r in fac.rank_log]
+        ld, sg = H.h2_logdet(h)
+        lo, so = fac.logdet()
+        assert sg[0] == so and abs(ld[0] - lo) <= 1e-9 * abs(lo)
+        b = synth.rhs(N, 1, 3)[:, 0].copy()
+        xo, _, _ = O.refine(op, fac, b, 1e-10, 30)
+        bt = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bt)
+        st, ach, it = H.h2_solve(h, bt, x, 1, N, 1e-10, 30)
+        assert st == H.H2_OK and rel(x.cpu().numpy(), xo) <= 1e-8
+    finally:
+        H.h2_destroy(h)

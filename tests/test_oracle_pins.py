@@ -338,3 +338,52 @@ def test_fill_in_set_matches_paper_example():
     fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fill_in_example.json")))
     got = O.fill_in_blocks(fx["near"], fx["row"])
     assert [list(p) for p in got] == fx["fill_in"]
+
+
+# ------------------------------------------------------- k-means tree -----
+def test_balanced_two_means_separates_two_blobs():
+    """Two equal, well separated blobs: the balanced 2-means split puts each
+    blob in one child, whichever blob the seeds start from."""
+    rng = np.random.default_rng(40)
+    A = rng.normal(0.0, 0.1, (50, 3))
+    B = rng.normal(0.0, 0.1, (50, 3)) + np.array([5.0, 0.0, 0.0])
+    X = np.vstack([A, B])[rng.permutation(100)]
+    order, it = O.balanced_two_means(X, np.arange(100))
+    left, right = set(order[:50].tolist()), set(order[50:].tolist())
+    blob_a = set(np.flatnonzero(X[:, 0] < 2.5).tolist())
+    assert left == blob_a or right == blob_a
+    assert it < 20
+
+
+def test_balanced_two_means_line_closed_form():
+    """Points 0, 1, 2 and 10, 11, 12 on a line: the split is {0,1,2} | {10,11,12}
+    in one Lloyd step, and the order within a child follows the key."""
+    X = np.zeros((6, 3))
+    X[:, 0] = [10.0, 0.0, 11.0, 2.0, 12.0, 1.0]
+    order, it = O.balanced_two_means(X, np.arange(6))
+    assert set(order[:3].tolist()) in ({1, 3, 5}, {0, 2, 4})
+    assert set(order[3:].tolist()) == {0, 1, 2, 3, 4, 5} - set(order[:3].tolist())
+
+
+def test_kmeans_tree_is_balanced_and_a_lloyd_fixed_point():
+    """Every split is balanced (floor(n/2) left) and, where the iteration
+    stopped before its cap, is a fixed point of the Lloyd step: recomputing
+    both centroids from the children and reassigning gives the same children."""
+    X = synth.surface_union(3000, 11)
+    L, perm, boxes = O.cluster_tree_kmeans(X, 100)
+    assert sorted(perm) == list(range(3000))
+    for l in range(L):
+        for p, (s, e) in enumerate(boxes[l]):
+            (s1, e1), (s2, e2) = boxes[l + 1][2 * p], boxes[l + 1][2 * p + 1]
+            assert s1 == s and e2 == e and e1 - s1 == (e - s) // 2
+            order, it = O.balanced_two_means(X, perm[s:e])
+            # the tree's children are that split (their order is refined further down)
+            assert set(order[:e1 - s1].tolist()) == set(perm[s1:e1].tolist())
+            if it < 20:
+                Pl, Pr = X[perm[s1:e1]], X[perm[s2:e2]]
+                c0, c1 = Pl.mean(0), Pr.mean(0)
+                idx = np.sort(perm[s:e])
+                P = X[idx]
+                key = ((P - c0) ** 2).sum(1) - ((P - c1) ** 2).sum(1)
+                left = set(idx[np.lexsort((idx, key))[:e1 - s1]].tolist())
+                assert left == set(perm[s1:e1].tolist())
