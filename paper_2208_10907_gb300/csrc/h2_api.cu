@@ -1955,13 +1955,65 @@ static void factor(Handle& h, int precision, int spd) {
         G = G2;
       }
       // far-field block row Gram K(cand, samples) K(cand, samples)^T
-      std::vector<KgramTask> kt;
-      for (int g = 0; g < nb; ++g) {
-        int m = (int)(sof[g + 1] - sof[g]);
-        if (m == 0) continue;
-        kt.push_back(KgramTask{dc + co[g], ds + sof[g], G + off[g], n[g], m, n[g], 1});
+      if (W == Prec::F64) {
+        std::vector<KgramTask> kt;
+        for (int g = 0; g < nb; ++g) {
+          int m = (int)(sof[g + 1] - sof[g]);
+          if (m == 0) continue;
+          kt.push_back(KgramTask{dc + co[g], ds + sof[g], G + off[g], n[g], m, n[g], 1});
+        }
+        run_kgram(W, kt, maxn, pts, h.kp, sc);
+      } else {
+        // mixed precision: each box's block row B = K(cand, samples) is
+        // evaluated once (FP32, chunks of boxes within the pair budget), its
+        // Gram B B^T formed by the batched tensor-core GEMM and added to G
+        float* Gfar = (float*)sc.alloc(NN * 4);
+        std::vector<int> boxes_far;
+        for (int g = 0; g < nb; ++g)
+          if (sof[g + 1] > sof[g]) boxes_far.push_back(g);
+        size_t b0 = 0;
+        while (b0 < boxes_far.size()) {
+          size_t b1 = b0, tot = 0;
+          std::vector<size_t> bo;
+          while (b1 < boxes_far.size()) {
+            const int g = boxes_far[b1];
+            const size_t need = ((size_t)n[g] * (sof[g + 1] - sof[g]) * 4 + 255) & ~size_t(255);
+            if (b1 > b0 && tot + need > pair_budget) break;
+            bo.push_back(tot);
+            tot += need;
+            ++b1;
+          }
+          char* Bb = (char*)pair_buf(tot);
+          std::vector<AsmTask> at;
+          GemmBatch gb;
+          int maxc = 0;
+          for (size_t q = b0; q < b1; ++q) {
+            const int g = boxes_far[q];
+            const int m = (int)(sof[g + 1] - sof[g]);
+            float* B = (float*)(Bb + bo[q - b0]);
+            at.push_back(AsmTask{B, dc + co[g], ds + sof[g], 0, 0, n[g], m, n[g]});
+            maxc = std::max(maxc, m);
+            gb.add1(Gfar + off[g], n[g], n[g], n[g], B, n[g], B, n[g], m, 1.0, 0.0, nullptr, 0, 2);
+          }
+          validate(at, 4);
+          {
+            double by = 0.0;
+            for (const AsmTask& a : at) by += 4.0 * a.nr * a.nc;
+            prof_note(0.0, by);
+          }
+          launch_assemble_far_f32(sc.up(at), (int)at.size(), maxc, pts, h.kp, sc.s);
+          prof_tag("basis_gram");
+          gb.run(W, false, false, sc);
+          prof_tag("basis");
+          b0 = b1;
+        }
+        std::vector<CopyTask> ca;
+        for (int g : boxes_far) ca.push_back(CopyTask{Gfar + off[g], G + off[g], n[g], n[g], n[g], n[g]});
+        if (!ca.empty()) {
+          prof_note(0.0, 12.0 * (double)NN);
+          launch_add_copy(sc.up(ca), (int)ca.size(), maxn, maxn, sc.s);
+        }
       }
-      run_kgram(W, kt, maxn, pts, h.kp, sc);
     }
     {
       // Rank tolerance of the Gram route.  In mixed precision the Gram

@@ -243,6 +243,10 @@ void launch_assemble(Prec p, const AsmTask* d, int ntasks, int maxr, int maxc, P
 void launch_copy(Prec src, Prec dst, bool transpose, const CopyTask* d, int ntasks, int maxr,
                  int maxc, cudaStream_t s);
 void launch_interp(Prec p, const InterpTask* d, int ntasks, cudaStream_t s);
+// FP32 far-field block rows (ridx: the box's points, at most NMAX; cidx: far samples)
+void launch_assemble_far_f32(const AsmTask* d, int ntasks, int maxc, Points pts, KParams kp, cudaStream_t s);
+// dst += src for FP32 src and FP64 dst blocks (CopyTask layout)
+void launch_add_copy(const CopyTask* d, int ntasks, int maxr, int maxc, cudaStream_t s);
 void launch_colnorm2(const double* X, int n, int nrhs, int64_t ld, double* out, cudaStream_t s);
 void launch_axpy_cols(double* Y, const double* X, int n, int nrhs, int64_t ldy, int64_t ldx,
                       double alpha, cudaStream_t s);

@@ -883,6 +883,41 @@ __global__ void __launch_bounds__(NT) assemble_kernel(const AsmTask* __restrict_
   }
 }
 
+// Far-field block row in FP32: out(i, j) = K(x[ridx[i]], x[cidx[j]]) with
+// coordinates taken relative to the box's first row point (one FP64
+// subtraction per point, the rest on the FP32 pipes); the columns are far
+// from the box, so the differences lose no relative accuracy.
+__global__ void __launch_bounds__(NT) assemble_far_f32_kernel(const AsmTask* __restrict__ tasks, Points pts,
+                                                              KParams kp) {
+  const AsmTask tk = tasks[blockIdx.x];
+  __shared__ float fx[NMAX], fy[NMAX], fz[NMAX];
+  __shared__ float sx[32], sy[32], sz[32];
+  const int g0 = tk.ridx[0];
+  const double cx = pts.x[g0], cy = pts.y[g0], cz = pts.z[g0];
+  for (int i = threadIdx.x; i < tk.nr; i += NT) {
+    const int g = tk.ridx[i];
+    fx[i] = (float)(pts.x[g] - cx);
+    fy[i] = (float)(pts.y[g] - cy);
+    fz[i] = (float)(pts.z[g] - cz);
+  }
+  float* out = reinterpret_cast<float*>(tk.out);
+  for (int j0 = blockIdx.y * 32; j0 < tk.nc; j0 += gridDim.y * 32) {
+    __syncthreads();
+    if (threadIdx.x < 32 && j0 + threadIdx.x < tk.nc) {
+      const int g = tk.cidx[j0 + threadIdx.x];
+      sx[threadIdx.x] = (float)(pts.x[g] - cx);
+      sy[threadIdx.x] = (float)(pts.y[g] - cy);
+      sz[threadIdx.x] = (float)(pts.z[g] - cz);
+    }
+    __syncthreads();
+    const int nj = min(32, tk.nc - j0);
+    for (int e = threadIdx.x; e < nj * tk.nr; e += NT) {
+      const int i = e % tk.nr, jj = e / tk.nr;
+      out[i + (long long)(j0 + jj) * tk.ld] = kernel_eval_ff(kp, fx[i] - sx[jj], fy[i] - sy[jj], fz[i] - sz[jj]);
+    }
+  }
+}
+
 template <typename TS, typename TD, bool TR>
 __global__ void __launch_bounds__(NT) copy_kernel(const CopyTask* __restrict__ tasks) {
   const CopyTask tk = tasks[blockIdx.x];
@@ -893,6 +928,18 @@ __global__ void __launch_bounds__(NT) copy_kernel(const CopyTask* __restrict__ t
     int i = (int)(e % tk.rows), j = (int)(e / tk.rows);
     TS v = TR ? s[j + (long long)i * tk.lds] : s[i + (long long)j * tk.lds];
     d[i + (long long)j * tk.ldd] = (TD)v;
+  }
+}
+
+// dst(i, j) += src(i, j): an FP32 block added into an FP64 one
+__global__ void __launch_bounds__(NT) add_copy_kernel(const CopyTask* __restrict__ tasks) {
+  const CopyTask tk = tasks[blockIdx.x];
+  const float* s = reinterpret_cast<const float*>(tk.src);
+  double* d = reinterpret_cast<double*>(tk.dst);
+  const long long cnt = (long long)tk.rows * tk.cols;
+  for (long long e = (long long)blockIdx.y * NT + threadIdx.x; e < cnt; e += (long long)gridDim.y * NT) {
+    const int i = (int)(e % tk.rows), j = (int)(e / tk.rows);
+    d[i + (long long)j * tk.ldd] += (double)s[i + (long long)j * tk.lds];
   }
 }
 
@@ -1152,6 +1199,14 @@ void launch_assemble(Prec p, const AsmTask* d, int ntasks, int maxr, int maxc, P
   H2_LAUNCH_CHECK();
 }
 
+void launch_assemble_far_f32(const AsmTask* d, int ntasks, int maxc, Points pts, KParams kp, cudaStream_t s) {
+  if (ntasks <= 0 || maxc <= 0) return;
+  ProfScope ps("assemble_far_f32", s);
+  dim3 grid(ntasks, std::min(64, (maxc + 31) / 32));
+  assemble_far_f32_kernel<<<grid, NT, 0, s>>>(d, pts, kp);
+  H2_LAUNCH_CHECK();
+}
+
 void launch_copy(Prec src, Prec dst, bool transpose, const CopyTask* d, int ntasks, int maxr, int maxc,
                  cudaStream_t s) {
   if (ntasks <= 0) return;
@@ -1168,6 +1223,16 @@ void launch_copy(Prec src, Prec dst, bool transpose, const CopyTask* d, int ntas
   else if (src == Prec::F32 && dst == Prec::F64) { H2_COPY(float, double) }
   else { H2_COPY(float, float) }
 #undef H2_COPY
+  H2_LAUNCH_CHECK();
+}
+
+void launch_add_copy(const CopyTask* d, int ntasks, int maxr, int maxc, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  ProfScope ps("add_copy", s);
+  long long cnt = (long long)maxr * maxc;
+  int gy = (int)std::min<long long>(64, (cnt + NT - 1) / NT);
+  if (gy < 1) gy = 1;
+  add_copy_kernel<<<dim3(ntasks, gy), NT, 0, s>>>(d);
   H2_LAUNCH_CHECK();
 }
 
