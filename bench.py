@@ -110,10 +110,24 @@ def cpu_oracle_sample(n_sample, repeats=1):
                        f"to N=2^20 (O(N) method); construct {np.median([t[0] for t in ts]):.2f} s not included")
 
 
-# DRAM traffic per launch of the dominant kernel, from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel@site; None
-# until a capture of the current kernel exists.
-NCU_TRAFFIC = {}
+# DRAM traffic of a kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), as bytes per algorithmic unit (flop or byte) of the
+# captured launch, keyed by kernel@site; a launch's traffic is that ratio x
+# its algorithmic units (the captures ran on N = 65 536, where the same
+# per-pair products run on the same block sizes).  Remove an entry when its
+# kernel changes.
+NCU_TRAFFIC = {
+    # tcgen05 GEMM, first leaf fill-in launch (8 192 products 256x256x256 =
+    # 274.9 GFLOP): 3.438 GB read + 2.108 GB write
+    "gemm_tc3xtf32@fillin": {"per_unit": (3.438254e9 + 2.108418e9) / 274.878e9,
+                             "source": "ncu dram__bytes_read/write.sum, N=65536 leaf fill-in launch, "
+                                       "scaled by flops per launch"},
+    # double-float near matvec, one launch over 4.61 GB of stored blocks:
+    # 4.62 GB read + 0.048 GB write
+    "symv_pairs_df@mv_near": {"per_unit": (4.62e9 + 0.048e9) / 4.61e9,
+                              "source": "ncu dram__bytes_read/write.sum, N=65536 near matvec, "
+                                        "scaled by algorithmic bytes per launch"},
+}
 
 FP32_PREFIX = ("gemm_f32", "kgram_f32", "getrf_f32", "trsm_f32", "hqr_f32")
 FP64_PREFIX = ("gemm_f64", "getrf_f64", "trsm_f64", "pchol_f64", "pqr_f64", "fold_f64", "hqr_f64", "kgram_f64")
@@ -143,11 +157,12 @@ def roofline_of(name, ks, pk, tot_ms):
         bound, unit, ach = "hbm", "GB/s", ks["bytes"] / secs / 1e9
         src = "measured HBM copy bandwidth" if pk else "fallback 6.8 TB/s"
     tr = NCU_TRAFFIC.get(name)
+    units = (ks["flops"] if bound != "hbm" else ks["bytes"]) / max(1, ks["launches"])
     return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-            "frac": ach / peak if peak else None, "traffic": tr["bytes_per_launch"] if tr else None,
+            "frac": ach / peak if peak else None, "traffic": tr["per_unit"] * units if tr else None,
             "traffic_source": tr["source"] if tr else None, "launches": ks["launches"],
             "ms_total": ks["ms"], "share": ks["ms"] / tot_ms, "per_launch_ms": ks["ms"] / max(1, ks["launches"]),
-            "algorithmic_per_launch": (ks["flops"] if bound != "hbm" else ks["bytes"]) / max(1, ks["launches"]),
+            "algorithmic_per_launch": units,
             "peak_source": src}
 
 

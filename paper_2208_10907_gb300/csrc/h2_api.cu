@@ -2313,7 +2313,15 @@ static void factor(Handle& h, int precision, int spd) {
           char* D = dest(g, j, ld);
           g2.add1(D, ld, r[g], r[j], V, r[g], Wp(j), r[j], r[j]);
         }
-        run_assemble(W, at, 256, maxc, pts, h.kp, sc);
+        if (W == Prec::F32) {   // far pairs: box-relative FP32 coordinates
+          validate(at, 4);
+          double by = 0.0;
+          for (const AsmTask& a : at) by += 4.0 * a.nr * a.nc;
+          prof_note(0.0, by);
+          launch_assemble_far_f32(sc.up(at), (int)at.size(), maxc, pts, h.kp, sc.s);
+        } else {
+          run_assemble(W, at, 256, maxc, pts, h.kp, sc);
+        }
         g1.run(W, false, false, sc);
         g2.run(W, false, true, sc);
         p0 = p1;
