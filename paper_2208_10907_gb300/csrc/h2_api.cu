@@ -479,7 +479,9 @@ static void run_getrf(Prec p, const std::vector<LuTask>& v, Scratch& sc) {
   validate(v, esz(p));
   double by = 0.0, f = work_getrf(v, esz(p), by);
   prof_note(f, by);
-  launch_getrf(p, sc.up(v), (int)v.size(), sc.s);
+  int maxm = 0;
+  for (const LuTask& t : v) maxm = std::max(maxm, t.m);
+  launch_getrf(p, sc.up(v), (int)v.size(), maxm, sc.s);
 }
 static void run_copy(Prec a, Prec b, bool tr, const std::vector<CopyTask>& v, int mr, int mc, Scratch& sc) {
   if (v.empty()) return;

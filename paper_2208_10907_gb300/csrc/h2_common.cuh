@@ -228,7 +228,7 @@ enum class Prec { F64 = 0, F32 = 1 };
 void launch_gemm(Prec p, const GemmTask* d_tasks, const GemmTerm* d_terms,
                  int ntasks, int maxM, int maxN, cudaStream_t s, bool inputs_f64 = false, int ksum = 0);
 std::string autotune_report();
-void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s);
+void launch_getrf(Prec p, const LuTask* d, int ntasks, int maxm, cudaStream_t s);
 void launch_trsm(Prec p, bool lower, bool unit, bool transA, const TrsmTask* d, int ntasks,
                  int maxnrhs, int maxn, cudaStream_t s);
 void launch_pchol(const CholTask* d, int ntasks, cudaStream_t s);

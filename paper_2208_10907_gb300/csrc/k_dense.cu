@@ -149,10 +149,162 @@ __global__ void __launch_bounds__(NT) getrf_kernel(const LuTask* __restrict__ ta
 }
 
 // ---------------------------------------------------------------------------
+// The same LU, blocked (m <= NMAX): left-looking over panels of LW = 32
+// columns held in shared memory.  A panel receives the row interchanges of
+// the columns before it, then their updates 32 columns at a time (the unit
+// lower triangle of the block, then the rows below it, whose L entries are
+// read from global memory once per row), then is factored in shared memory;
+// its interchanges are applied to the finished columns to its left.  Every
+// entry receives the same updates in the same order and form (x - l*u) as in
+// the unblocked kernel above, so the two give identical results; the
+// trailing matrix is no longer read and written at every step.
+// ---------------------------------------------------------------------------
+constexpr int LW = 32, LWP = LW + 1;
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 2) getrf_blocked_kernel(const LuTask* __restrict__ tasks) {
+  const LuTask tk = tasks[blockIdx.x];
+  T* A = reinterpret_cast<T*>(tk.A);
+  const int m = tk.m, nc = tk.nc, lda = tk.lda;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ T s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_piv[NMAX];
+  __shared__ unsigned char s_skip[NMAX];     // column k's pivot was zero / NaN: it updates nothing
+  __shared__ T Ld[LW * LWP];                 // unit lower triangle of one finished 32-column block
+  extern __shared__ unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);     // panel, m x LW, row-major with pitch LWP
+  bool singular = false;
+  for (int p0 = 0; p0 < nc; p0 += LW) {
+    const int w = min(LW, nc - p0);
+    for (int e = tid; e < m * w; e += NT) {
+      const int i = e % m, c = e / m;
+      P[i * LWP + c] = A[i + (long long)(p0 + c) * lda];
+    }
+    __syncthreads();
+    // interchanges of the columns to the left, in order (one thread per column)
+    if (tid < w) {
+      for (int k = 0; k < p0; ++k) {
+        const int p = s_piv[k];
+        if (p != k) {
+          const T a = P[k * LWP + tid];
+          P[k * LWP + tid] = P[p * LWP + tid];
+          P[p * LWP + tid] = a;
+        }
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < p0; q += LW) {
+      for (int e = tid; e < LW * LW; e += NT) {
+        const int r = e % LW, k = e / LW;
+        Ld[r * LWP + k] = A[(q + r) + (long long)(q + k) * lda];
+      }
+      __syncthreads();
+      // rows q .. q+31: each warp solves whole columns, lanes = rows
+      for (int c = warp; c < w; c += NT / 32) {
+        for (int k = 0; k < LW - 1; ++k) {
+          if (!s_skip[q + k] && lane > k)
+            P[(q + lane) * LWP + c] = P[(q + lane) * LWP + c] - Ld[lane * LWP + k] * P[(q + k) * LWP + c];
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // rows below the block, each row in two halves of 16 columns
+      const int nbelow = m - q - LW;
+      for (int e = tid; e < 2 * nbelow; e += NT) {
+        const int r = q + LW + e % nbelow, h = (e / nbelow) * (LW / 2);
+        T lv[LW], acc[LW / 2];
+#pragma unroll
+        for (int k = 0; k < LW; ++k) lv[k] = A[r + (long long)(q + k) * lda];
+#pragma unroll
+        for (int c = 0; c < LW / 2; ++c) acc[c] = P[r * LWP + h + c];
+#pragma unroll
+        for (int k = 0; k < LW; ++k) {
+          if (s_skip[q + k]) continue;
+#pragma unroll
+          for (int c = 0; c < LW / 2; ++c) acc[c] = acc[c] - lv[k] * P[(q + k) * LWP + h + c];
+        }
+#pragma unroll
+        for (int c = 0; c < LW / 2; ++c) P[r * LWP + h + c] = acc[c];
+      }
+      __syncthreads();
+    }
+    // factor the panel in shared memory
+    for (int c = 0; c < w; ++c) {
+      const int k = p0 + c;
+      T best = (T)-1;
+      int bi = 0x7fffffff;
+      for (int i = k + tid; i < m; i += NT) {
+        const T v = tabs(P[i * LWP + c]);
+        if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+      }
+      T pv;
+      int p;
+      block_argmax(best, bi, s_val, s_idx, pv, p);
+      if (tk.spd) p = k;
+      if (p < k || p >= m) {
+        p = k;
+        if (tid == 0 && tk.info) atomicCAS(tk.info, 0, k + 1);
+      }
+      if (tid == 0) {
+        s_piv[k] = p;
+        tk.piv[k] = p;
+      }
+      if (p != k) {
+        for (int j = tid; j < w; j += NT) {
+          const T a = P[k * LWP + j];
+          P[k * LWP + j] = P[p * LWP + j];
+          P[p * LWP + j] = a;
+        }
+      }
+      __syncthreads();
+      const T akk = P[k * LWP + c];
+      if (akk == (T)0 || akk != akk || (tk.spd && akk < (T)0)) {
+        if (!singular && tid == 0 && tk.info) atomicCAS(tk.info, 0, k + 1);
+        singular = true;
+        if (tid == 0) s_skip[k] = 1;
+        __syncthreads();
+        continue;
+      }
+      if (tid == 0) s_skip[k] = 0;
+      const T inv = (T)1 / akk;
+      for (int i = k + 1 + tid; i < m; i += NT) P[i * LWP + c] = P[i * LWP + c] * inv;
+      __syncthreads();
+      const int rows = m - k - 1, cols = w - c - 1;
+      for (int e = tid; e < rows * cols; e += NT) {
+        const int i = k + 1 + e % rows, j = c + 1 + e / rows;
+        P[i * LWP + j] = P[i * LWP + j] - P[i * LWP + c] * P[k * LWP + j];
+      }
+      __syncthreads();
+    }
+    // the panel's interchanges on the finished columns to its left, then
+    // the panel back to global memory
+    for (int j = tid; j < p0; j += NT) {
+      for (int c = 0; c < w; ++c) {
+        const int k = p0 + c, p = s_piv[k];
+        if (p != k) {
+          const T a = A[k + (long long)j * lda];
+          A[k + (long long)j * lda] = A[p + (long long)j * lda];
+          A[p + (long long)j * lda] = a;
+        }
+      }
+    }
+    for (int e = tid; e < m * w; e += NT) {
+      const int i = e % m, c = e / m;
+      A[i + (long long)(p0 + c) * lda] = P[i * LWP + c];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Left triangular solve B <- op(A)^-1 B on a 32-column chunk held in shared
 // memory; A read from global memory.  Optional row interchanges first.
+// Column by column (FP64): each step divides x_j (non-unit diagonal) and
+// updates the rows beyond j with column j of op(A).
 // ---------------------------------------------------------------------------
 constexpr int TS_COLS = 32;
+
 
 template <typename T, bool LOWER, bool UNIT, bool TRANSA>
 __global__ void __launch_bounds__(NT) trsm_kernel(const TrsmTask* __restrict__ tasks) {
@@ -232,6 +384,103 @@ __global__ void __launch_bounds__(NT) trsm_kernel(const TrsmTask* __restrict__ t
     }
   }
   for (int e = threadIdx.x; e < n * nc; e += NT) {
+    int i = e % n, cc = e / n;
+    B[i + (long long)cc * tk.ldb] = X[i * LDX + cc];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same solve blocked by 32 rows (FP32): the
+// diagonal block of op(A) is staged in shared memory and solved by warps
+// (one right-hand side column at a time, lanes = rows), then the rows beyond
+// it take the block's 32 updates with their op(A) entries read from global
+// memory once.  Every entry receives the updates x -= a x_j in the order of
+// the column-by-column substitution (j ascending for lower, descending for
+// upper; the division by a_jj first when the diagonal is not unit).
+// ---------------------------------------------------------------------------
+
+template <typename T, bool LOWER, bool UNIT, bool TRANSA>
+__global__ void __launch_bounds__(NT, 2) trsm_blocked_kernel(const TrsmTask* __restrict__ tasks) {
+  const TrsmTask tk = tasks[blockIdx.x];
+  const int c0 = blockIdx.y * TS_COLS;
+  if (c0 >= tk.nrhs) return;
+  const int nc = min(TS_COLS, tk.nrhs - c0);
+  const int n = tk.n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const T* A = reinterpret_cast<const T*>(tk.A);
+  T* B = reinterpret_cast<T*>(tk.B) + (long long)c0 * tk.ldb;
+  extern __shared__ unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);   // n x (TS_COLS+1)
+  const int LDX = TS_COLS + 1;
+  __shared__ T Ad[32 * 33];                // diagonal block of op(A)
+  for (int e = tid; e < n * nc; e += NT) {
+    int i = e % n, c = e / n;
+    X[i * LDX + c] = B[i + (long long)c * tk.ldb];
+  }
+  __syncthreads();
+  if (tk.piv) {
+    if (tid < nc) {
+      int c = tid;
+      for (int k = 0; k < n; ++k) {
+        int p = tk.piv[k];
+        if (p != k) {
+          T a = X[k * LDX + c];
+          X[k * LDX + c] = X[p * LDX + c];
+          X[p * LDX + c] = a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  auto aij = [&](int i, int j) -> T {
+    return TRANSA ? A[j + (long long)i * tk.lda] : A[i + (long long)j * tk.lda];
+  };
+  const int nblk = (n + 31) / 32;
+  for (int bb = 0; bb < nblk; ++bb) {
+    const int blk = LOWER ? bb : nblk - 1 - bb;
+    const int b = blk * 32, bw = min(32, n - b);
+    for (int e = tid; e < 32 * 32; e += NT) {
+      const int r = e % 32, k = e / 32;
+      Ad[r * 33 + k] = (r < bw && k < bw) ? aij(b + r, b + k) : (T)0;
+    }
+    __syncthreads();
+    // the diagonal block
+    for (int c = warp; c < nc; c += NT / 32) {
+      for (int t = 0; t < bw; ++t) {
+        const int k = LOWER ? t : bw - 1 - t;
+        if (!UNIT) {
+          if (lane == k) X[(b + k) * LDX + c] /= Ad[k * 33 + k];
+          __syncwarp();
+        }
+        const T xk = X[(b + k) * LDX + c];
+        if (LOWER ? (lane > k && lane < bw) : (lane < k))
+          X[(b + lane) * LDX + c] = X[(b + lane) * LDX + c] - Ad[lane * 33 + k] * xk;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // the rows beyond the block: below it (lower) or above it (upper)
+    const int r_lo = LOWER ? b + bw : 0, nr = LOWER ? n - r_lo : b;
+    for (int e = tid; e < 2 * nr; e += NT) {   // each row in two halves of 16 columns
+      const int r = r_lo + e % nr, h = (e / nr) * (TS_COLS / 2);
+      T av[32], acc[TS_COLS / 2];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) av[k] = k < bw ? aij(r, b + k) : (T)0;
+#pragma unroll
+      for (int c = 0; c < TS_COLS / 2; ++c) acc[c] = X[r * LDX + h + c];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int k = LOWER ? t : 31 - t;
+        if (k >= bw) continue;
+#pragma unroll
+        for (int c = 0; c < TS_COLS / 2; ++c) acc[c] = acc[c] - av[k] * X[(b + k) * LDX + h + c];
+      }
+#pragma unroll
+      for (int c = 0; c < TS_COLS / 2; ++c) X[r * LDX + h + c] = acc[c];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * nc; e += NT) {
     int i = e % n, cc = e / n;
     B[i + (long long)cc * tk.ldb] = X[i * LDX + cc];
   }
@@ -923,10 +1172,27 @@ __global__ void __launch_bounds__(NT) copy_kernel(const CopyTask* __restrict__ t
   const CopyTask tk = tasks[blockIdx.x];
   const TS* s = reinterpret_cast<const TS*>(tk.src);
   TD* d = reinterpret_cast<TD*>(tk.dst);
+  if (!TR) {
+    // column by column: a column takes the rows rounded up to whole warps
+    // (at most all threads), the CTA's threads cover several columns at
+    // once, and the CTAs of a task take interleaved column groups (no index
+    // division per element)
+    const int R = tk.rows;
+    const int tpc = R >= NT ? NT : ((R + 31) & ~31);
+    const int cpp = NT / tpc;
+    const int sub = threadIdx.x / tpc, i0 = threadIdx.x % tpc;
+    if (sub >= cpp) return;
+    for (int j = blockIdx.y * cpp + sub; j < tk.cols; j += gridDim.y * cpp) {
+      const TS* sc = s + (long long)j * tk.lds;
+      TD* dc = d + (long long)j * tk.ldd;
+      for (int i = i0; i < R; i += tpc) dc[i] = (TD)sc[i];
+    }
+    return;
+  }
   const long long cnt = (long long)tk.rows * tk.cols;
   for (long long e = (long long)blockIdx.y * NT + threadIdx.x; e < cnt; e += (long long)gridDim.y * NT) {
     int i = (int)(e % tk.rows), j = (int)(e / tk.rows);
-    TS v = TR ? s[j + (long long)i * tk.lds] : s[i + (long long)j * tk.lds];
+    TS v = s[j + (long long)i * tk.lds];
     d[i + (long long)j * tk.ldd] = (TD)v;
   }
 }
@@ -1090,12 +1356,27 @@ __global__ void logdet_kernel(const LuTask* __restrict__ tasks, double* out_log,
 }  // namespace
 
 // ------------------------------------------------------------ launchers ----
-void launch_getrf(Prec p, const LuTask* d, int ntasks, cudaStream_t s) {
+void launch_getrf(Prec p, const LuTask* d, int ntasks, int maxm, cudaStream_t s) {
   if (ntasks <= 0) return;
   ProfScope ps(p == Prec::F64 ? "getrf_f64" : "getrf_f32", s);
-  // panel rows up to a few thousand (root panels): smem = (m + nc) * sizeof(T)
-  // is sized by the caller's maximum via the attribute below.
-  size_t smem = (size_t)(8192 + NMAX) * (p == Prec::F64 ? 8 : 4);
+  if (maxm <= NMAX) {
+    // blocked kernel: one m x 32 panel in shared memory
+    const size_t smem = (size_t)std::max(maxm, 1) * LWP * (p == Prec::F64 ? 8 : 4);
+    if (p == Prec::F64) {
+      H2_CUDA(cudaFuncSetAttribute(getrf_blocked_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+      getrf_blocked_kernel<double><<<ntasks, NT, smem, s>>>(d);
+    } else {
+      H2_CUDA(cudaFuncSetAttribute(getrf_blocked_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+      getrf_blocked_kernel<float><<<ntasks, NT, smem, s>>>(d);
+    }
+    H2_LAUNCH_CHECK();
+    return;
+  }
+  // taller panels: unblocked kernel, column k and row k staged in shared
+  // memory
+  size_t smem = (size_t)2 * maxm * (p == Prec::F64 ? 8 : 4);   // nc <= m
   if (p == Prec::F64) {
     H2_CUDA(cudaFuncSetAttribute(getrf_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     getrf_kernel<double><<<ntasks, NT, smem, s>>>(d);
@@ -1111,9 +1392,15 @@ static void trsm_dispatch(bool lower, bool unit, bool transA, const TrsmTask* d,
                           cudaStream_t s) {
 #define H2_TRSM_CASE(L, U, TR)                                                                        \
   if (lower == L && unit == U && transA == TR) {                                                      \
-    H2_CUDA(cudaFuncSetAttribute(trsm_kernel<T, L, U, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)smem));                                                         \
-    trsm_kernel<T, L, U, TR><<<grid, NT, smem, s>>>(d);                                               \
+    if constexpr (sizeof(T) == 4) {                                                                   \
+      H2_CUDA(cudaFuncSetAttribute(trsm_blocked_kernel<T, L, U, TR>,                                  \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));          \
+      trsm_blocked_kernel<T, L, U, TR><<<grid, NT, smem, s>>>(d);                                     \
+    } else {                                                                                          \
+      H2_CUDA(cudaFuncSetAttribute(trsm_kernel<T, L, U, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                   (int)smem));                                                       \
+      trsm_kernel<T, L, U, TR><<<grid, NT, smem, s>>>(d);                                             \
+    }                                                                                                 \
     return;                                                                                           \
   }
   H2_TRSM_CASE(true, true, false)
