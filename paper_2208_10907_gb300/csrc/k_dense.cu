@@ -1182,7 +1182,20 @@ __global__ void __launch_bounds__(NT) copy_kernel(const CopyTask* __restrict__ t
     const int cpp = NT / tpc;
     const int sub = threadIdx.x / tpc, i0 = threadIdx.x % tpc;
     if (sub >= cpp) return;
-    for (int j = blockIdx.y * cpp + sub; j < tk.cols; j += gridDim.y * cpp) {
+    const int js = gridDim.y * cpp;
+    int j = blockIdx.y * cpp + sub;
+    // four columns per pass: their loads are in flight together
+    for (; j + 3 * js < tk.cols; j += 4 * js) {
+      for (int i = i0; i < R; i += tpc) {
+        const TS v0 = s[i + (long long)j * tk.lds], v1 = s[i + (long long)(j + js) * tk.lds];
+        const TS v2 = s[i + (long long)(j + 2 * js) * tk.lds], v3 = s[i + (long long)(j + 3 * js) * tk.lds];
+        d[i + (long long)j * tk.ldd] = (TD)v0;
+        d[i + (long long)(j + js) * tk.ldd] = (TD)v1;
+        d[i + (long long)(j + 2 * js) * tk.ldd] = (TD)v2;
+        d[i + (long long)(j + 3 * js) * tk.ldd] = (TD)v3;
+      }
+    }
+    for (; j < tk.cols; j += js) {
       const TS* sc = s + (long long)j * tk.lds;
       TD* dc = d + (long long)j * tk.ldd;
       for (int i = i0; i < R; i += tpc) dc[i] = (TD)sc[i];
