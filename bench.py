@@ -315,6 +315,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64-path steps (0 = skip)")
     ap.add_argument("--kernel-table", action="store_true", help="print the per-kernel event table to stderr")
+    ap.add_argument("--max-rank", type=int, default=None,
+                    help="rank cap per box (default: the workload's 128; at most 256)")
     ap.add_argument("--partition", default="bisection", choices=["bisection", "kmeans"],
                     help="cluster tree of the headline workload (the default is the workload's bisection)")
     ap.add_argument("--workload", default="surfaces1m", choices=["surfaces1m", "batched64"],
@@ -335,7 +337,9 @@ def main():
     dist_init(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if args.max_rank is not None:
+        W["max_rank"] = args.max_rank
     n = max(4096, int(W["n"] * args.scale))
     X = synth.surface_union(n, W["seed"])
     b_host = synth.rhs(n, 1, W["rhs_seed"])[:, 0].copy()
