@@ -6,7 +6,8 @@
 // close to FP32 accuracy (the dropped A_lo B_lo term is ~2^-22 relative).
 //
 // One CTA computes a 128 x 256 output tile of one task (MMA N sized to the
-// task, a multiple of 16).  Operands are staged by the CTA itself
+// task, a multiple of 16), or a 128 x 128 tile when no output of the launch
+// is wider than 128 columns.  Operands are staged by the CTA itself
 // (per-term transposition, bounds and the hi/lo split happen in the load
 // path) into the canonical no-swizzle K-major shared-memory layout: 8-row x
 // 16-byte core matrices, adjacent along K at LBO = 128 bytes, 8-row groups
@@ -174,8 +175,15 @@ __device__ __forceinline__ uint32_t instr_desc_n(int n_mma) {
   return d;
 }
 
-__global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restrict__ tasks,
+// TNB_ = 256: one 128 x 256 output tile per CTA; TNB_ = 128 (launches whose
+// outputs are at most 128 columns wide, e.g. the r-wide projections): a
+// 128 x 128 tile with half the B staging, TMEM and shared memory.
+template <int TNB_>
+__global__ void __launch_bounds__(NTH, TNB_ == 128 ? 3 : 2) tc_gemm_kernel(const GemmTask* __restrict__ tasks,
                                                          const GemmTerm* __restrict__ terms, int* err) {
+  constexpr int BBYTES_ = TNB_ * BK * 4;
+  constexpr int STAGE_ = 2 * ABYTES + 2 * BBYTES_;
+  constexpr int CHALF = TNB_ / 2;                      // epilogue columns per warp group
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* base = smem + ((1024 - (smem_u32(smem) & 1023)) & 1023);
   __shared__ uint64_t mbar[NSTAGE];
@@ -184,17 +192,17 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
 
   const GemmTask tk = tasks[blockIdx.x];
   const int tiles_m = (tk.M + TM - 1) / TM;
-  const int tiles_n = (tk.N + TNB - 1) / TNB;
+  const int tiles_n = (tk.N + TNB_ - 1) / TNB_;
   const int tile = blockIdx.y;
   if (tile >= tiles_m * tiles_n) return;
-  const int i0 = (tile % tiles_m) * TM, j0 = (tile / tiles_m) * TNB;
-  const int ncols = min(TNB, tk.N - j0);
+  const int i0 = (tile % tiles_m) * TM, j0 = (tile / tiles_m) * TNB_;
+  const int ncols = min(TNB_, tk.N - j0);
   const int n_mma = ((ncols + 15) / 16) * 16;          // MMA N: multiple of 16, <= 256
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TNB));
+                 "r"(TNB_));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
   for (int t = tk.t0; t < tk.t0 + tk.nt; ++t) nchunks += (terms[t].K + BK - 1) / BK;
 
   Stage<TM> ra;
-  Stage<TNB> rb;
+  Stage<TNB_> rb;
   int cur_t = tk.t0, cur_k = 0;
   GemmTerm tm{};
   auto load_chunk = [&](int t, int k0) {
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
     // op(A)(i, k): TRA -> A[k + i*lda] (contiguous along k)
     stage_load<TM>(ra, reinterpret_cast<const float*>(g.A), g.lda, TRA, i0, tk.M, k0, g.K);
     // B operand rows are output columns n: op(B)(k, n) = TRB ? B[n + k*ldb] : B[k + n*ldb]
-    stage_load<TNB>(rb, reinterpret_cast<const float*>(g.B), g.ldb, !TRB, j0, tk.N, k0, g.K);
+    stage_load<TNB_>(rb, reinterpret_cast<const float*>(g.B), g.ldb, !TRB, j0, tk.N, k0, g.K);
   };
   bool contigA = false, contigB = false;
   if (nchunks > 0) {
@@ -237,10 +245,10 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
   int committed = 0;                                   // chunks whose MMAs were committed (thread 0)
   for (int c = 0; c < nchunks; ++c) {
     const int st = c % NSTAGE;
-    unsigned char* sA_hi = base + st * STAGE_BYTES;
+    unsigned char* sA_hi = base + st * STAGE_;
     unsigned char* sA_lo = sA_hi + ABYTES;
     unsigned char* sB_hi = sA_lo + ABYTES;
-    unsigned char* sB_lo = sB_hi + BBYTES;
+    unsigned char* sB_lo = sB_hi + BBYTES_;
     if (c >= NSTAGE) {
       // the MMAs of chunk c - NSTAGE read this stage: one thread waits for
       // them (bounded), the others sleep in the barrier instead of polling
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
       __syncthreads();
     }
     stage_store<TM>(ra, contigA, sA_hi, sA_lo);
-    stage_store<TNB>(rb, contigB, sB_hi, sB_lo);
+    stage_store<TNB_>(rb, contigB, sB_hi, sB_lo);
     // prefetch the next chunk into registers while the tensor core works
     {
       int nt = cur_t, nk = cur_k + BK;
@@ -325,10 +333,10 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
   const float* Cin = reinterpret_cast<const float*>(tk.Cin);
   if (!s_fail && nchunks > 0) {
     const int lane_grp = warp & 3;             // TMEM lanes 32*lane_grp .. +31
-    const int col_half = warp >> 2;            // columns [0,128) or [128,256)
+    const int col_half = warp >> 2;            // columns [0, CHALF) or [CHALF, TNB_)
     const int row = i0 + lane_grp * 32 + lane;
 #pragma unroll 1
-    for (int c0 = col_half * 128; c0 < col_half * 128 + 128; c0 += 8) {
+    for (int c0 = col_half * CHALF; c0 < col_half * CHALF + CHALF; c0 += 8) {
       if (c0 >= n_mma) break;
       uint32_t r[8];
       uint32_t taddr = tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)c0;
@@ -350,7 +358,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
       }
     }
   } else if (!s_fail) {
-    for (int e = tid; e < TM * TNB; e += NTH) {
+    for (int e = tid; e < TM * TNB_; e += NTH) {
       int r = i0 + e % TM, c = j0 + e / TM;
       if (r < tk.M && c < tk.N) {
         float v = 0.f;
@@ -362,7 +370,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_gemm_kernel(const GemmTask* __restr
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TNB));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TNB_));
   }
 }
 
@@ -380,15 +388,27 @@ static int* tc_err_flag() {
 void launch_gemm_tc(const GemmTask* d_tasks, const GemmTerm* d_terms, int ntasks, int maxM, int maxN,
                     cudaStream_t s) {
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return;
-  const size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
-  static bool attr = false;
-  if (!attr) {
-    H2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
-  dim3 grid(ntasks, ((maxM + TM - 1) / TM) * ((maxN + TNB - 1) / TNB));
   ProfScope ps("gemm_tc3xtf32", s);
-  tc_gemm_kernel<<<grid, NTH, smem, s>>>(d_tasks, d_terms, tc_err_flag());
+  if (maxN <= 128) {
+    constexpr int W = 128;
+    const size_t smem = (size_t)NSTAGE * (2 * ABYTES + 2 * W * BK * 4) + 1024;
+    static bool attr = false;
+    if (!attr) {
+      H2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+    dim3 grid(ntasks, ((maxM + TM - 1) / TM) * ((maxN + W - 1) / W));
+    tc_gemm_kernel<W><<<grid, NTH, smem, s>>>(d_tasks, d_terms, tc_err_flag());
+  } else {
+    const size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
+    static bool attr = false;
+    if (!attr) {
+      H2_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<TNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+    dim3 grid(ntasks, ((maxM + TM - 1) / TM) * ((maxN + TNB - 1) / TNB));
+    tc_gemm_kernel<TNB><<<grid, NTH, smem, s>>>(d_tasks, d_terms, tc_err_flag());
+  }
   H2_LAUNCH_CHECK();
 }
 
