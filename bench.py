@@ -414,6 +414,7 @@ def main():
         for k_, v_ in ks_[:48]:
             print(f"{k_:32s} launches {v_['launches']:6d} ms {v_['ms']:10.2f} ({100 * v_['ms'] / tot_:5.1f}%) "
                   f"GFLOP {v_['flops'] / 1e9:10.1f} GB {v_['bytes'] / 1e9:9.2f}", file=sys.stderr)
+        print("GEMM autotuner choices:", json.dumps(stats.get("autotune", [])), file=sys.stderr)
 
     # ---- roofline of every kernel (algorithmic flops or bytes per launch
     # over its event time); the dominant one goes in "roofline"
