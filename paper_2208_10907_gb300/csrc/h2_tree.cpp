@@ -54,17 +54,8 @@ static void balanced_two_means(const double* P, int64_t* first, int64_t* last) {
   if (n < 2) return;
   std::vector<int64_t> idx(first, last);
   std::sort(idx.begin(), idx.end());
-  auto mean = [&](const std::vector<int64_t>& v, double c[3]) {
-    double sx = 0.0, sy = 0.0, sz = 0.0;
-    for (int64_t i : v) {
-      sx += P[3 * i];
-      sy += P[3 * i + 1];
-      sz += P[3 * i + 2];
-    }
-    c[0] = sx / (double)v.size();
-    c[1] = sy / (double)v.size();
-    c[2] = sz / (double)v.size();
-  };
+  // idx is in increasing caller index, so a position q in it orders the
+  // points exactly as their caller indices do
   auto d2 = [&](int64_t i, const double c[3]) {
     const double dx = P[3 * i] - c[0], dy = P[3 * i + 1] - c[1], dz = P[3 * i + 2] - c[2];
     return (dx * dx + dy * dy) + dz * dz;
@@ -81,33 +72,54 @@ static void balanced_two_means(const double* P, int64_t* first, int64_t* last) {
     }
     return best;
   };
-  double m[3], c0[3], c1[3];
-  mean(idx, m);
+  double m[3] = {0.0, 0.0, 0.0}, c0[3], c1[3];
+  {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t i : idx) {
+      sx += P[3 * i];
+      sy += P[3 * i + 1];
+      sz += P[3 * i + 2];
+    }
+    m[0] = sx / (double)n;
+    m[1] = sy / (double)n;
+    m[2] = sz / (double)n;
+  }
   const int64_t a = farthest(m);
   for (int k = 0; k < 3; ++k) c0[k] = P[3 * a + k];
   const int64_t b = farthest(c0);
   for (int k = 0; k < 3; ++k) c1[k] = P[3 * b + k];
   const int64_t h = n / 2;
-  std::vector<std::pair<double, int64_t>> key(n);
-  std::vector<int64_t> left, prev, right;
-  auto assign = [&]() {
-    for (int64_t q = 0; q < n; ++q) key[q] = {d2(idx[q], c0) - d2(idx[q], c1), idx[q]};
-    std::sort(key.begin(), key.end());
+  std::vector<std::pair<double, int64_t>> key(n);   // (|x-c0|^2 - |x-c1|^2, position)
+  std::vector<char> left(n, 0), prev(n, 0);
+  auto keys = [&]() {
+    for (int64_t q = 0; q < n; ++q) key[q] = {d2(idx[q], c0) - d2(idx[q], c1), q};
   };
   for (int it = 0; it < 20; ++it) {
-    assign();
-    left.clear();
-    right.clear();
-    for (int64_t q = 0; q < n; ++q) (q < h ? left : right).push_back(key[q].second);
-    std::sort(left.begin(), left.end());
-    std::sort(right.begin(), right.end());
+    // the left child is the set of the h smallest keys (ties -> lower
+    // caller index); only the set matters until the last step
+    keys();
+    std::nth_element(key.begin(), key.begin() + h, key.end());
+    std::fill(left.begin(), left.end(), 0);
+    for (int64_t q = 0; q < h; ++q) left[key[q].second] = 1;
     if (it > 0 && left == prev) break;
     prev = left;
-    mean(left, c0);
-    mean(right, c1);
-    if (it == 19) assign();
+    // children's means, summed in increasing caller index
+    double sl[3] = {0.0, 0.0, 0.0}, sr[3] = {0.0, 0.0, 0.0};
+    for (int64_t q = 0; q < n; ++q) {
+      double* acc = left[q] ? sl : sr;
+      acc[0] += P[3 * idx[q]];
+      acc[1] += P[3 * idx[q] + 1];
+      acc[2] += P[3 * idx[q] + 2];
+    }
+    for (int k = 0; k < 3; ++k) {
+      c0[k] = sl[k] / (double)h;
+      c1[k] = sr[k] / (double)(n - h);
+    }
+    if (it == 19) keys();
   }
-  for (int64_t q = 0; q < n; ++q) first[q] = key[q].second;
+  // final order: the keys of the last assignment, fully sorted
+  std::sort(key.begin(), key.end());
+  for (int64_t q = 0; q < n; ++q) first[q] = idx[key[q].second];
 }
 
 Tree build_tree(const double* P, int64_t N, int leaf, double eta, int partition) {
