@@ -89,7 +89,12 @@ typedef struct {
 
 /* Precision of the factorization.  The rank decisions (pivoted QR/ID), the
  * redundant-block LU/Cholesky pivots and the refinement residual are FP64
- * in every mode. */
+ * in every mode.  H2_MIXED runs the dense products (fill-ins, projections,
+ * Schur updates, far-field Gram) in split 3xTF32 on the tensor cores: each
+ * FP32 operand is split into two TF32 parts and three products accumulate
+ * in FP32.  There is no split-BF16 mode: three BF16 parts need six
+ * products for the same accuracy, at twice the TF32 rate, i.e. the same
+ * tensor-core time. */
 typedef enum { H2_FP64 = 0, H2_MIXED = 1 } h2_precision;
 
 typedef struct h2_handle_* h2_handle;
